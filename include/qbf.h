@@ -1,0 +1,178 @@
+/*
+ * qbf.h -- C ABI of libqubobf, exhaustive QUBO minimisation on one GB300.
+ *
+ * Method: arXiv 2310.19373, "Faster QUBO Brute-Force Solving using Gray Code".
+ *   f_Q(x) = x^T Q x over x in {0,1}^n                              (Eq. 1)
+ *   all 2^n vectors are visited in reflected Gray-code order, so step t
+ *   flips bit CTZ(t) (Section 2.2) and the objective moves by the one-bit
+ *   delta of Eq. 2 instead of being re-evaluated;                    (Alg. 1)
+ *   the top bits of x are fixed per worker and the sub-walks are combined
+ *   by a minimum (Section 3.1).
+ *
+ * Conventions shared by every entry point
+ * ---------------------------------------
+ *  - Q is dense, row-major, n x n.  f(x) = sum_{i,j} Q_ij x_i x_j uses every
+ *    entry, which is Eq. 1 when Q is upper triangular.
+ *  - A state is reported by its natural index idx(x) = sum_i x_i 2^i
+ *    (x_i = bit i, as in the naive method of Section 3).
+ *  - Ties go to the lowest natural index.  (Algorithm 1 keeps the first
+ *    state met in Gray order; this library reports the unique answer that
+ *    does not depend on the enumeration order.)
+ *  - Every entry point returns an int status (QBF_OK = 0) and never aborts.
+ *    On error, qbf_last_error_string() describes the failure (thread-local).
+ *  - Pointers named *_dev must be device memory of the current device;
+ *    pointers named *_host are host memory.  The caller owns all buffers;
+ *    the library keeps no pointer after a call returns.
+ *  - `stream` is a cudaStream_t passed as void* (NULL = legacy default
+ *    stream).  Work is enqueued on it; calls that fill a host struct wait
+ *    for that stream before returning.
+ *  - The library keeps a per-device scratch pool (grow-only, reused across
+ *    calls, freed by qbf_release).  Calls are serialised by an internal lock.
+ */
+#ifndef QBF_H
+#define QBF_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define QBF_MAX_N 48    /* largest n for qbf_solve                        */
+#define QBF_MAX_TOPK 64 /* largest top_k                                  */
+
+/* element type of Q */
+typedef enum {
+    QBF_F64 = 0, /* double                                                 */
+    QBF_F32 = 1, /* float                                                  */
+    QBF_I32 = 2, /* int32_t                                                */
+    QBF_I16 = 3  /* int16_t                                                */
+} qbf_dtype;
+
+/* status codes */
+enum {
+    QBF_OK = 0,
+    QBF_EINVAL = 1,     /* bad argument (null pointer, n out of range ...)  */
+    QBF_ENONFINITE = 2, /* Q holds NaN or Inf                               */
+    QBF_EDTYPE = 3,     /* unknown dtype                                    */
+    QBF_ECUDA = 4,      /* a CUDA call failed                               */
+    QBF_EOVERFLOW = 5,  /* more candidate states than the scratch can hold  */
+    QBF_ECANCELED = 6,
+    QBF_ENOTIMPL = 7,
+    QBF_ERANGE = 8      /* integer Q whose sum |Q_ij| does not fit in int32 */
+};
+
+/* walk kernels */
+enum {
+    QBF_VARIANT_AUTO = 0,
+    QBF_VARIANT_FIELD = 1, /* per-thread local-field vector g in registers  */
+    QBF_VARIANT_SPLIT = 2  /* field split into lane-invariant + lane parts  */
+};
+
+typedef struct {
+    int top_k;          /* number of best states to return, 1..64 (0 -> 1)  */
+    int variant;        /* QBF_VARIANT_*                                     */
+    int prefix_bits;    /* bits fixed per GPU thread (Section 3.1's m);
+                           -1 = chosen by the planner                        */
+    int fix_bits;       /* restrict the search to states whose top fix_bits
+                           variables x_{n-fix_bits..n-1} equal fix_value;
+                           0 = whole space                                   */
+    uint64_t fix_value;
+    int timing;         /* 1: time the main walk kernel with CUDA events on
+                           `stream` and report it in qbf_result.walk_seconds */
+    int reserved[7];
+} qbf_options;
+
+typedef struct {
+    double min_value;   /* min f; FP64 canonical sum for float Q, exact for
+                           integer Q (see README of the oracle order)       */
+    uint64_t argmin;    /* lowest natural index attaining min_value         */
+    int top_k;          /* entries filled in topk_* (<= requested)          */
+    double topk_value[QBF_MAX_TOPK];   /* ascending by (value, index)       */
+    uint64_t topk_index[QBF_MAX_TOPK];
+    int scale_bits;     /* sigma: the walk runs on round(Q * 2^sigma)       */
+    double error_bound; /* half-width of the certification window, in units
+                           of f (0 for integer Q)                          */
+    uint64_t n_candidates; /* states rescored in FP64 / int64               */
+    int prefix_bits;    /* k actually used                                  */
+    int suffix_bits;    /* n - k                                            */
+    int variant;        /* walk kernel actually used                        */
+    int walk_launches;  /* launches of the main walk kernel in this call    */
+    double walk_seconds;/* device time of the main walk kernel(s) when
+                           opt->timing was set, else 0                      */
+    int kernel_launches;/* kernels this call launched                       */
+    int reserved[3];
+} qbf_result;
+
+/* Fill *opt with defaults (top_k = 1, auto variant, auto prefix width). */
+void qbf_default_options(qbf_options *opt);
+
+/*
+ * qbf_solve -- minimum, lowest-index argmin and optional top-k of x^T Q x.
+ *
+ * Q_dev : device pointer, n*n elements of `dtype`, row-major.  Read only.
+ * n     : 1 .. QBF_MAX_N.
+ * opt   : NULL for defaults.
+ * out   : host struct, filled when the call returns QBF_OK.
+ *
+ * Float Q is walked exactly on a fixed-point image round(Q * 2^sigma) in
+ * int32; every state whose fixed-point value lies within the rounding bound
+ * of the best is rescored with the FP64 canonical sum, so the reported min
+ * and argmin are those of the FP64 canonical objective.  Integer Q is walked
+ * exactly (QBF_ERANGE when sum |Q_ij| >= 2^31).
+ * Errors: QBF_EINVAL, QBF_EDTYPE, QBF_ENONFINITE, QBF_ERANGE, QBF_EOVERFLOW
+ * (the certification window holds more than 2^22 states, e.g. massive exact
+ * ties with top_k > 1), QBF_ECUDA.
+ */
+int qbf_solve(const void *Q_dev, int n, int dtype, const qbf_options *opt, qbf_result *out,
+              void *stream);
+
+/* Same as qbf_solve with Q in host memory: copies Q to the device on
+ * `stream` first (the end-to-end path). */
+int qbf_solve_host(const void *Q_host, int n, int dtype, const qbf_options *opt,
+                   qbf_result *out, void *stream);
+
+/*
+ * qbf_walk_trace -- debug walk that records every visited state.
+ *
+ * Runs the split walk with 2^prefix_bits threads over the whole space
+ * (n <= 24) and writes, for visit slot s = p * 2^(n-k) + t (thread p, step
+ * t), the natural index of the state it visits to idx_dev[s] and its
+ * fixed-point objective round(Q * 2^sigma) evaluated by the walk to
+ * val_dev[s].  *sigma_out receives sigma.  idx_dev and val_dev hold 2^n
+ * entries each.  Used to check Eq. 2's incremental update and the Gray
+ * enumeration state by state.
+ */
+int qbf_walk_trace(const void *Q_dev, int n, int dtype, int prefix_bits, uint64_t *idx_dev,
+                   int64_t *val_dev, int *sigma_out, void *stream);
+
+/*
+ * qbf_alu_microbench -- measures one ALU instruction class on every SM.
+ *
+ * op: 0 IADD3, 1 IMNMX, 2 3-input integer min, 3 FADD, 4 FFMA, 5 FMNMX,
+ *     6 3-input FMNMX, 7 packed FADD (f32x2), 8 IADD3+IMNMX pair,
+ *     9 FADD+FMNMX pair.
+ * Writes scalar lane operations per SM clock per SM to *ops_per_clk_sm (a
+ * packed f32x2 add counts two, each instruction of a pair counts one), the
+ * SM clock seen during the run to *sm_mhz and the elapsed device time to
+ * *seconds.  Allocates and frees its own small buffers.  Used for the
+ * roofline denominator of the walk.
+ */
+int qbf_alu_microbench(int op, double *ops_per_clk_sm, double *sm_mhz, double *seconds,
+                       void *stream);
+
+/* Human-readable description of the last error on this thread. */
+const char *qbf_last_error_string(void);
+
+/* Free the library's scratch pools on every device it touched. */
+int qbf_release(void);
+
+/* Library version as an integer (major*10000 + minor*100 + patch). */
+int qbf_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* QBF_H */

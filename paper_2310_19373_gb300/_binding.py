@@ -1,0 +1,254 @@
+"""ctypes binding of libqubobf (include/qbf.h).
+
+Argument marshalling only: every step of a solve runs in the CUDA library.
+The low-level functions keep the C names; ``solve`` is a convenience wrapper
+that takes a torch tensor (device or host) and returns a ``Solution``.
+If the library has not been built this module raises on first use -- there
+is no CPU fallback.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from dataclasses import dataclass, field
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "_build", "libqubobf.so")
+
+QBF_F64, QBF_F32, QBF_I32, QBF_I16 = 0, 1, 2, 3
+QBF_OK, QBF_EINVAL, QBF_ENONFINITE, QBF_EDTYPE, QBF_ECUDA = 0, 1, 2, 3, 4
+QBF_EOVERFLOW, QBF_ECANCELED, QBF_ENOTIMPL, QBF_ERANGE = 5, 6, 7, 8
+QBF_VARIANT_AUTO, QBF_VARIANT_FIELD, QBF_VARIANT_SPLIT = 0, 1, 2
+QBF_MAX_N = 48
+QBF_MAX_TOPK = 64
+
+STATUS_NAMES = {
+    0: "QBF_OK", 1: "QBF_EINVAL", 2: "QBF_ENONFINITE", 3: "QBF_EDTYPE", 4: "QBF_ECUDA",
+    5: "QBF_EOVERFLOW", 6: "QBF_ECANCELED", 7: "QBF_ENOTIMPL", 8: "QBF_ERANGE",
+}
+
+
+class QbfOptions(ctypes.Structure):
+    _fields_ = [
+        ("top_k", ctypes.c_int),
+        ("variant", ctypes.c_int),
+        ("prefix_bits", ctypes.c_int),
+        ("fix_bits", ctypes.c_int),
+        ("fix_value", ctypes.c_uint64),
+        ("timing", ctypes.c_int),
+        ("reserved", ctypes.c_int * 7),
+    ]
+
+
+class QbfResult(ctypes.Structure):
+    _fields_ = [
+        ("min_value", ctypes.c_double),
+        ("argmin", ctypes.c_uint64),
+        ("top_k", ctypes.c_int),
+        ("topk_value", ctypes.c_double * QBF_MAX_TOPK),
+        ("topk_index", ctypes.c_uint64 * QBF_MAX_TOPK),
+        ("scale_bits", ctypes.c_int),
+        ("error_bound", ctypes.c_double),
+        ("n_candidates", ctypes.c_uint64),
+        ("prefix_bits", ctypes.c_int),
+        ("suffix_bits", ctypes.c_int),
+        ("variant", ctypes.c_int),
+        ("walk_launches", ctypes.c_int),
+        ("walk_seconds", ctypes.c_double),
+        ("kernel_launches", ctypes.c_int),
+        ("reserved", ctypes.c_int * 3),
+    ]
+
+
+class QbfError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"{STATUS_NAMES.get(status, status)}: {msg}")
+        self.status = status
+
+
+_lib = None
+
+_VP = ctypes.c_void_p
+_SIGS = {
+    "qbf_default_options": (None, [ctypes.POINTER(QbfOptions)]),
+    "qbf_solve": (ctypes.c_int, [_VP, ctypes.c_int, ctypes.c_int, ctypes.POINTER(QbfOptions),
+                                 ctypes.POINTER(QbfResult), _VP]),
+    "qbf_solve_host": (ctypes.c_int, [_VP, ctypes.c_int, ctypes.c_int,
+                                      ctypes.POINTER(QbfOptions), ctypes.POINTER(QbfResult), _VP]),
+    "qbf_walk_trace": (ctypes.c_int, [_VP, ctypes.c_int, ctypes.c_int, ctypes.c_int, _VP, _VP,
+                                      ctypes.POINTER(ctypes.c_int), _VP]),
+    "qbf_alu_microbench": (ctypes.c_int, [ctypes.c_int, ctypes.POINTER(ctypes.c_double),
+                                          ctypes.POINTER(ctypes.c_double),
+                                          ctypes.POINTER(ctypes.c_double), _VP]),
+    "qbf_last_error_string": (ctypes.c_char_p, []),
+    "qbf_release": (ctypes.c_int, []),
+    "qbf_version": (ctypes.c_int, []),
+}
+
+
+def lib():
+    """Load libqubobf.so (built by ``__graft_entry__.build()``); raise if it is missing."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError(
+                f"{LIB_PATH} is missing: build the CUDA library first "
+                "(python -c 'import __graft_entry__ as g; g.build()')")
+        L = ctypes.CDLL(LIB_PATH)
+        for name, (res, args) in _SIGS.items():
+            fn = getattr(L, name)
+            fn.restype = res
+            fn.argtypes = args
+        _lib = L
+    return _lib
+
+
+def _check(rc: int):
+    if rc != QBF_OK:
+        raise QbfError(rc, lib().qbf_last_error_string().decode(errors="replace"))
+
+
+# ---- same names as the C ABI ---------------------------------------------
+
+
+def qbf_default_options() -> QbfOptions:
+    o = QbfOptions()
+    lib().qbf_default_options(ctypes.byref(o))
+    return o
+
+
+def qbf_solve(Q_dev: int, n: int, dtype: int, opt: QbfOptions | None, stream: int | None = None):
+    out = QbfResult()
+    rc = lib().qbf_solve(_VP(Q_dev), n, dtype, ctypes.byref(opt) if opt is not None else None,
+                         ctypes.byref(out), _VP(stream or 0))
+    _check(rc)
+    return out
+
+
+def qbf_solve_host(Q_host: int, n: int, dtype: int, opt: QbfOptions | None,
+                   stream: int | None = None):
+    out = QbfResult()
+    rc = lib().qbf_solve_host(_VP(Q_host), n, dtype,
+                              ctypes.byref(opt) if opt is not None else None,
+                              ctypes.byref(out), _VP(stream or 0))
+    _check(rc)
+    return out
+
+
+def qbf_walk_trace(Q_dev: int, n: int, dtype: int, prefix_bits: int, idx_dev: int, val_dev: int,
+                   stream: int | None = None) -> int:
+    sigma = ctypes.c_int()
+    rc = lib().qbf_walk_trace(_VP(Q_dev), n, dtype, prefix_bits, _VP(idx_dev), _VP(val_dev),
+                              ctypes.byref(sigma), _VP(stream or 0))
+    _check(rc)
+    return sigma.value
+
+
+def qbf_alu_microbench(op: int, stream: int | None = None):
+    ops = ctypes.c_double()
+    mhz = ctypes.c_double()
+    sec = ctypes.c_double()
+    rc = lib().qbf_alu_microbench(op, ctypes.byref(ops), ctypes.byref(mhz), ctypes.byref(sec),
+                                  _VP(stream or 0))
+    _check(rc)
+    return ops.value, mhz.value, sec.value
+
+
+def qbf_last_error_string() -> str:
+    return lib().qbf_last_error_string().decode(errors="replace")
+
+
+def qbf_release() -> None:
+    _check(lib().qbf_release())
+
+
+def qbf_version() -> int:
+    return lib().qbf_version()
+
+
+# ---- torch convenience ---------------------------------------------------
+
+
+def dtype_code(t) -> int:
+    import torch
+
+    m = {torch.float64: QBF_F64, torch.float32: QBF_F32, torch.int32: QBF_I32,
+         torch.int16: QBF_I16}
+    if t.dtype not in m:
+        raise QbfError(QBF_EDTYPE, f"unsupported dtype {t.dtype}")
+    return m[t.dtype]
+
+
+@dataclass
+class Solution:
+    min_value: float
+    argmin: int
+    topk_values: list = field(default_factory=list)
+    topk_indices: list = field(default_factory=list)
+    scale_bits: int = 0
+    error_bound: float = 0.0
+    n_candidates: int = 0
+    prefix_bits: int = 0
+    suffix_bits: int = 0
+    variant: int = 0
+    walk_launches: int = 0
+    walk_seconds: float = 0.0
+    kernel_launches: int = 0
+
+    def x(self, n: int):
+        """argmin as a 0/1 list, x_i = bit i of the natural index."""
+        return [(self.argmin >> i) & 1 for i in range(n)]
+
+
+def _solution(r: QbfResult) -> Solution:
+    k = r.top_k
+    return Solution(r.min_value, int(r.argmin), list(r.topk_value[:k]),
+                    [int(v) for v in r.topk_index[:k]], r.scale_bits, r.error_bound,
+                    int(r.n_candidates), r.prefix_bits, r.suffix_bits, r.variant,
+                    r.walk_launches, r.walk_seconds, r.kernel_launches)
+
+
+def make_options(top_k: int = 1, variant: int = QBF_VARIANT_AUTO, prefix_bits: int = -1,
+                 fix_bits: int = 0, fix_value: int = 0, timing: bool = False) -> QbfOptions:
+    o = qbf_default_options()
+    o.timing = 1 if timing else 0
+    o.top_k = top_k
+    o.variant = variant
+    o.prefix_bits = prefix_bits
+    o.fix_bits = fix_bits
+    o.fix_value = fix_value
+    return o
+
+
+def solve(Q, top_k: int = 1, variant: int = QBF_VARIANT_AUTO, prefix_bits: int = -1,
+          fix_bits: int = 0, fix_value: int = 0, stream=None, timing: bool = False) -> Solution:
+    """Minimise x^T Q x for a square torch tensor Q (CUDA or CPU memory)."""
+    import torch
+
+    if Q.dim() != 2 or Q.shape[0] != Q.shape[1]:
+        raise QbfError(QBF_EINVAL, "Q must be a square matrix")
+    Q = Q.contiguous()
+    n = Q.shape[0]
+    opt = make_options(top_k, variant, prefix_bits, fix_bits, fix_value, timing)
+    if Q.is_cuda:
+        s = stream if stream is not None else torch.cuda.current_stream(Q.device).cuda_stream
+        with torch.cuda.device(Q.device):
+            r = qbf_solve(Q.data_ptr(), n, dtype_code(Q), opt, s)
+    else:
+        s = stream if stream is not None else torch.cuda.current_stream().cuda_stream
+        r = qbf_solve_host(Q.data_ptr(), n, dtype_code(Q), opt, s)
+    return _solution(r)
+
+
+def walk_trace(Q, prefix_bits: int):
+    """Every state the walk visits, as (natural index, fixed-point value, sigma) tensors."""
+    import torch
+
+    Q = Q.contiguous()
+    n = Q.shape[0]
+    idx = torch.empty(1 << n, dtype=torch.int64, device=Q.device)
+    val = torch.empty(1 << n, dtype=torch.int64, device=Q.device)
+    s = torch.cuda.current_stream(Q.device).cuda_stream
+    sigma = qbf_walk_trace(Q.data_ptr(), n, dtype_code(Q), prefix_bits, idx.data_ptr(),
+                           val.data_ptr(), s)
+    return idx, val, sigma

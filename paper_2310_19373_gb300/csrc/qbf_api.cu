@@ -1,0 +1,493 @@
+// qbf_api.cu -- host runtime of libqubobf: argument checks, planning, scratch
+// pool and the launch sequence of one solve.
+//
+// One solve (qbf_solve) enqueues on the caller's stream:
+//   prepare_kernel        A1  fixed-point image of Q, certification window
+//   tables_kernel         A1  lane-invariant walk records + in-block corrections
+//   corrections -> constant bank (device-to-device copy)
+//   reset_counters_kernel
+//   walk (MIN)            A2-A4  every prefix's minimum and the global minimum
+//   threshold_kernel      A5/A7  tau = k-th smallest prefix minimum + W
+//   flag_kernel           A6  prefixes that can hold a winning state
+//   walk (EMIT)           A6  re-walk of those prefixes, emitting candidates
+//   rescore_kernel        A6  FP64 canonical / exact int64 value per candidate
+//   select_kernel         A5/A7  top-k by (value, natural index)
+// then copies the small result back and waits for the stream.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cstdio>
+#include <cstring>
+#include <mutex>
+#include <string>
+#include <vector>
+
+#include "qbf.h"
+#include "qbf_internal.cuh"
+#include "qbf_kernels.cuh"
+
+using namespace qbf;
+
+namespace {
+
+thread_local std::string g_err;
+std::mutex g_mu;
+
+int set_err(int code, const std::string &msg)
+{
+    g_err = msg;
+    return code;
+}
+
+int cuda_err(cudaError_t e, const char *where)
+{
+    g_err = std::string(where) + ": " + cudaGetErrorString(e);
+    return QBF_ECUDA;
+}
+
+#define QBF_CUDA(call, where)                                                                    \
+    do {                                                                                         \
+        cudaError_t qbf_e_ = (call);                                                             \
+        if (qbf_e_ != cudaSuccess)                                                               \
+            return cuda_err(qbf_e_, where);                                                      \
+    } while (0)
+
+struct Pool {
+    void *dev = nullptr;
+    size_t bytes = 0;
+    void *host = nullptr;  // pinned staging for the result
+    size_t hbytes = 0;
+};
+std::vector<Pool> g_pools;
+
+size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
+
+struct Layout {
+    size_t plan, ctr, res, kbuf, recs, pmin, flagged, cand, vals, qcopy, total;
+};
+
+Layout make_layout(size_t nrec, size_t npref, size_t qbytes, bool need_cand)
+{
+    Layout L;
+    size_t o = 0;
+    L.plan = o;
+    o = align256(o + sizeof(Plan));
+    L.ctr = o;
+    o = align256(o + sizeof(Counters));
+    L.res = o;
+    o = align256(o + sizeof(DevResult));
+    L.kbuf = o;
+    o = align256(o + sizeof(int) * 128);
+    L.recs = o;
+    o = align256(o + sizeof(Rec) * std::max<size_t>(nrec, 2));
+    L.pmin = o;
+    o = align256(o + sizeof(int) * npref);
+    L.flagged = o;
+    o = align256(o + sizeof(unsigned) * npref);
+    L.cand = o;
+    o = align256(o + (need_cand ? sizeof(unsigned long long) * kCandCap : 0));
+    L.vals = o;
+    o = align256(o + (need_cand ? sizeof(long long) * kCandCap : 0));
+    L.qcopy = o;
+    o = align256(o + qbytes);
+    L.total = o;
+    return L;
+}
+
+int pool_get(size_t bytes, size_t hbytes, Pool **out)
+{
+    int dev = 0;
+    QBF_CUDA(cudaGetDevice(&dev), "cudaGetDevice");
+    if ((int)g_pools.size() <= dev)
+        g_pools.resize(dev + 1);
+    Pool &P = g_pools[dev];
+    if (P.bytes < bytes) {
+        if (P.dev) {
+            QBF_CUDA(cudaDeviceSynchronize(), "cudaDeviceSynchronize");
+            cudaFree(P.dev);
+            P.dev = nullptr;
+            P.bytes = 0;
+        }
+        QBF_CUDA(cudaMalloc(&P.dev, bytes), "cudaMalloc(scratch)");
+        P.bytes = bytes;
+    }
+    if (P.hbytes < hbytes) {
+        if (P.host)
+            cudaFreeHost(P.host);
+        P.host = nullptr;
+        P.hbytes = 0;
+        QBF_CUDA(cudaMallocHost(&P.host, hbytes), "cudaMallocHost");
+        P.hbytes = hbytes;
+    }
+    *out = &P;
+    return QBF_OK;
+}
+
+size_t dtype_size(int dt)
+{
+    switch (dt) {
+    case QBF_F64: return 8;
+    case QBF_F32: return 4;
+    case QBF_I32: return 4;
+    case QBF_I16: return 2;
+    default: return 0;
+    }
+}
+
+int num_sms()
+{
+    int dev = 0, nsm = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess)
+        return 1;
+    if (cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+        return 1;
+    return nsm > 0 ? nsm : 1;
+}
+
+// Suffix width walked per thread when the caller leaves it to the planner:
+// small n -> few long walks are not worth it, large n -> 2^24 prefixes keep the
+// per-prefix set-up below 1% of the walk and give a fine-grained work queue.
+int auto_suffix_bits(int n)
+{
+    if (n <= 10)
+        return n;
+    int ns = n - 24;
+    if (ns < 10)
+        ns = 10;
+    return ns;
+}
+
+struct Geo {
+    int n, k, ns, R, M, q;
+    unsigned long long p_lo, p_hi;
+};
+
+int plan_geometry(int n, const qbf_options &o, Geo *g)
+{
+    int k;
+    if (o.prefix_bits >= 0) {
+        k = o.prefix_bits;
+        if (k > n - 1 || k > 28)
+            return set_err(QBF_EINVAL, "prefix_bits must be in [0, min(n-1, 28)]");
+    } else {
+        k = n - auto_suffix_bits(n);
+    }
+    if (o.fix_bits < 0 || o.fix_bits > n - 1)
+        return set_err(QBF_EINVAL, "fix_bits must be in [0, n-1]");
+    if (o.fix_bits > 0 && (o.fix_value >> o.fix_bits) != 0)
+        return set_err(QBF_EINVAL, "fix_value has bits above fix_bits");
+    if (k < o.fix_bits)
+        k = o.fix_bits;
+    g->n = n;
+    g->k = k;
+    g->ns = n - k;
+    g->R = std::min(kRMax, g->ns);
+    g->M = g->ns - g->R;
+    g->q = std::min(g->M, 10);
+    if (o.fix_bits > 0) {
+        g->p_lo = o.fix_value << (k - o.fix_bits);
+        g->p_hi = (o.fix_value + 1) << (k - o.fix_bits);
+    } else {
+        g->p_lo = 0;
+        g->p_hi = 1ull << k;
+    }
+    return QBF_OK;
+}
+
+int walk_grid(int R, int mode, int n, int ns, unsigned long long nitems)
+{
+    const size_t smem = walk_smem_bytes(n, ns, R);
+    const int bps = walk_blocks_per_sm(R, mode, smem);
+    const long long full = (long long)num_sms() * bps;
+    const long long need = (long long)((nitems + (kWalkThreads / 32) - 1) / (kWalkThreads / 32));
+    return (int)std::max<long long>(1, std::min(full, need));
+}
+
+// Enqueue prepare + tables + constant-bank copy + counter reset.
+int enqueue_prepare(const void *Q, int n, int dtype, const Geo &g, char *base, const Layout &L,
+                    cudaStream_t s)
+{
+    Plan *plan = (Plan *)(base + L.plan);
+    prepare_kernel<<<1, 256, 0, s>>>(Q, n, dtype, plan);
+    QBF_CUDA(cudaGetLastError(), "prepare_kernel");
+    const unsigned nrec = 1u << g.M;
+    tables_kernel<<<(nrec + 255) / 256, 256, 0, s>>>(plan, g.ns, g.R, (Rec *)(base + L.recs), nrec,
+                                                    (int *)(base + L.kbuf));
+    QBF_CUDA(cudaGetLastError(), "tables_kernel");
+    QBF_CUDA(copy_corrections((const int *)(base + L.kbuf), s), "corrections to constant bank");
+    reset_counters_kernel<<<1, 32, 0, s>>>((Counters *)(base + L.ctr));
+    QBF_CUDA(cudaGetLastError(), "reset_counters_kernel");
+    return QBF_OK;
+}
+
+int check_common(const void *Q, int n, int dtype, qbf_result *out)
+{
+    if (!Q || !out)
+        return set_err(QBF_EINVAL, "null pointer argument");
+    if (n < 1 || n > QBF_MAX_N)
+        return set_err(QBF_EINVAL, "n must be in [1, 48]");
+    if (dtype_size(dtype) == 0)
+        return set_err(QBF_EDTYPE, "unknown dtype");
+    return QBF_OK;
+}
+
+int solve_locked(const void *Q, bool host_q, int n, int dtype, const qbf_options *opt_in,
+                 qbf_result *out, cudaStream_t s)
+{
+    int rc = check_common(Q, n, dtype, out);
+    if (rc)
+        return rc;
+    qbf_options o;
+    qbf_default_options(&o);
+    if (opt_in)
+        o = *opt_in;
+    if (o.top_k == 0)
+        o.top_k = 1;
+    if (o.top_k < 1 || o.top_k > QBF_MAX_TOPK)
+        return set_err(QBF_EINVAL, "top_k must be in [1, 64]");
+    if (o.variant != QBF_VARIANT_AUTO && o.variant != QBF_VARIANT_SPLIT)
+        return set_err(QBF_ENOTIMPL, "requested walk variant is not built");
+    Geo g;
+    if ((rc = plan_geometry(n, o, &g)))
+        return rc;
+
+    const unsigned long long npref = g.p_hi - g.p_lo;
+    const size_t qbytes = host_q ? dtype_size(dtype) * n * n : 0;
+    const Layout L = make_layout(1u << g.M, npref, qbytes, true);
+    Pool *P = nullptr;
+    if ((rc = pool_get(L.total, sizeof(DevResult) + sizeof(Plan), &P)))
+        return rc;
+    char *base = (char *)P->dev;
+    const void *Qdev = Q;
+    if (host_q) {
+        QBF_CUDA(cudaMemcpyAsync(base + L.qcopy, Q, qbytes, cudaMemcpyHostToDevice, s),
+                 "copy Q to device");
+        Qdev = base + L.qcopy;
+    }
+    if ((rc = enqueue_prepare(Qdev, n, dtype, g, base, L, s)))
+        return rc;
+
+    Plan *plan = (Plan *)(base + L.plan);
+    Counters *ctr = (Counters *)(base + L.ctr);
+    const Rec *recs = (const Rec *)(base + L.recs);
+    int *pmin = (int *)(base + L.pmin);
+    unsigned *flagged = (unsigned *)(base + L.flagged);
+    unsigned long long *cand = (unsigned long long *)(base + L.cand);
+    long long *vals = (long long *)(base + L.vals);
+    DevResult *dres = (DevResult *)(base + L.res);
+
+    // A2-A4: MIN walk over every prefix
+    WalkArgs a;
+    memset(&a, 0, sizeof(a));
+    a.n = n;
+    a.ns = g.ns;
+    a.p_lo = g.p_lo;
+    a.p_hi = g.p_hi;
+    a.nitems = (npref + 31) / 32;
+    a.ctr = ctr;
+    a.pmin = pmin;
+    cudaEvent_t ev[2] = {nullptr, nullptr};
+    if (o.timing) {
+        QBF_CUDA(cudaEventCreate(&ev[0]), "cudaEventCreate");
+        QBF_CUDA(cudaEventCreate(&ev[1]), "cudaEventCreate");
+        QBF_CUDA(cudaEventRecord(ev[0], s), "cudaEventRecord");
+    }
+    QBF_CUDA(launch_walk(kModeMin, g.R, plan, recs, a, walk_grid(g.R, kModeMin, n, g.ns, a.nitems), s),
+             "walk (min)");
+    if (o.timing)
+        QBF_CUDA(cudaEventRecord(ev[1], s), "cudaEventRecord");
+
+    // A5-A7: threshold, flags, re-walk of flagged prefixes, rescoring, selection
+    threshold_kernel<<<1, 1024, 0, s>>>(plan, pmin, npref, o.top_k, ctr);
+    QBF_CUDA(cudaGetLastError(), "threshold_kernel");
+    const bool is_int = (dtype == QBF_I32 || dtype == QBF_I16);
+    // With W = 0 (integer Q) and top_k = 1 the lowest flagged prefix holds the
+    // answer; float Q with an all-zero image also has W = 0 and is exact.
+    const int lowest_mode = (o.top_k == 1 && is_int) ? 1 : 0;
+    {
+        const int fb = (int)std::min<unsigned long long>((npref + 255) / 256, 4096);
+        flag_kernel<<<fb, 256, 0, s>>>(plan, pmin, npref, g.p_lo, lowest_mode, flagged, ctr);
+        QBF_CUDA(cudaGetLastError(), "flag_kernel");
+    }
+    WalkArgs e = a;
+    e.ns = g.ns - g.q;
+    e.q = g.q;
+    e.lowest_mode = lowest_mode;
+    e.flagged = flagged;
+    e.cand = cand;
+    e.cand_cap = kCandCap;
+    e.pmin = nullptr;
+    // the number of flagged prefixes is only known on the device: size the
+    // persistent grid for the worst case, idle warps exit at once
+    const unsigned long long max_items = ((lowest_mode ? 1ull : npref) << g.q) / 32 + 1;
+    QBF_CUDA(launch_walk(kModeEmit, g.R, plan, recs, e, walk_grid(g.R, kModeEmit, n, e.ns, max_items), s),
+             "walk (emit)");
+    rescore_kernel<<<256, 256, 0, s>>>(plan, Qdev, n, dtype, cand, ctr, kCandCap, vals);
+    QBF_CUDA(cudaGetLastError(), "rescore_kernel");
+    select_kernel<<<1, 1024, 0, s>>>(plan, cand, vals, ctr, kCandCap, o.top_k, dres);
+    QBF_CUDA(cudaGetLastError(), "select_kernel");
+
+    char *h = (char *)P->host;
+    QBF_CUDA(cudaMemcpyAsync(h, dres, sizeof(DevResult), cudaMemcpyDeviceToHost, s), "copy result");
+    QBF_CUDA(cudaMemcpyAsync(h + sizeof(DevResult), plan, offsetof(Plan, lin), cudaMemcpyDeviceToHost, s),
+             "copy plan");
+    QBF_CUDA(cudaStreamSynchronize(s), "solve");
+    float walk_ms = 0.f;
+    if (o.timing) {
+        cudaEventElapsedTime(&walk_ms, ev[0], ev[1]);
+        cudaEventDestroy(ev[0]);
+        cudaEventDestroy(ev[1]);
+    }
+    const DevResult *R = (const DevResult *)h;
+    const Plan *PH = (const Plan *)(h + sizeof(DevResult));
+    if (PH->status != QBF_OK) {
+        if (PH->status == QBF_ENONFINITE)
+            return set_err(QBF_ENONFINITE, "Q holds NaN or Inf");
+        if (PH->status == QBF_ERANGE)
+            return set_err(QBF_ERANGE, "integer Q: sum |Q_ij| must stay below 2^31");
+        return set_err(PH->status, "prepare failed");
+    }
+    if (R->status == QBF_EOVERFLOW)
+        return set_err(QBF_EOVERFLOW, "more than 2^22 states inside the certification window");
+    if (R->status != QBF_OK || R->count < 1)
+        return set_err(QBF_ECUDA, "internal error: no candidate state selected");
+
+    memset(out, 0, sizeof(*out));
+    out->top_k = R->count;
+    for (int i = 0; i < R->count; ++i) {
+        out->topk_value[i] = R->topk_value[i];
+        out->topk_index[i] = R->topk_index[i];
+    }
+    out->min_value = R->topk_value[0];
+    out->argmin = R->topk_index[0];
+    out->scale_bits = PH->sigma;
+    out->error_bound = is_int ? 0.0 : PH->error_bound;
+    out->n_candidates = R->n_candidates;
+    out->prefix_bits = g.k;
+    out->suffix_bits = g.ns;
+    out->variant = QBF_VARIANT_SPLIT;
+    out->walk_launches = 1;
+    // prepare, tables, reset, walk(min), threshold, flag, walk(emit), rescore, select
+    out->kernel_launches = 9;
+    out->walk_seconds = walk_ms * 1e-3;
+    return QBF_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+void qbf_default_options(qbf_options *opt)
+{
+    if (!opt)
+        return;
+    memset(opt, 0, sizeof(*opt));
+    opt->top_k = 1;
+    opt->variant = QBF_VARIANT_AUTO;
+    opt->prefix_bits = -1;
+}
+
+int qbf_solve(const void *Q_dev, int n, int dtype, const qbf_options *opt, qbf_result *out,
+              void *stream)
+{
+    std::lock_guard<std::mutex> lk(g_mu);
+    return solve_locked(Q_dev, false, n, dtype, opt, out, (cudaStream_t)stream);
+}
+
+int qbf_solve_host(const void *Q_host, int n, int dtype, const qbf_options *opt,
+                   qbf_result *out, void *stream)
+{
+    std::lock_guard<std::mutex> lk(g_mu);
+    return solve_locked(Q_host, true, n, dtype, opt, out, (cudaStream_t)stream);
+}
+
+int qbf_walk_trace(const void *Q_dev, int n, int dtype, int prefix_bits, uint64_t *idx_dev,
+                   int64_t *val_dev, int *sigma_out, void *stream)
+{
+    std::lock_guard<std::mutex> lk(g_mu);
+    cudaStream_t s = (cudaStream_t)stream;
+    if (!Q_dev || !idx_dev || !val_dev || !sigma_out)
+        return set_err(QBF_EINVAL, "null pointer argument");
+    if (n < 1 || n > 24)
+        return set_err(QBF_EINVAL, "trace needs 1 <= n <= 24");
+    if (dtype_size(dtype) == 0)
+        return set_err(QBF_EDTYPE, "unknown dtype");
+    qbf_options o;
+    qbf_default_options(&o);
+    o.prefix_bits = prefix_bits;
+    Geo g;
+    int rc = plan_geometry(n, o, &g);
+    if (rc)
+        return rc;
+    const unsigned long long npref = g.p_hi - g.p_lo;
+    const Layout L = make_layout(1u << g.M, npref, 0, false);
+    Pool *P = nullptr;
+    if ((rc = pool_get(L.total, sizeof(DevResult) + sizeof(Plan), &P)))
+        return rc;
+    char *base = (char *)P->dev;
+    if ((rc = enqueue_prepare(Q_dev, n, dtype, g, base, L, s)))
+        return rc;
+    WalkArgs a;
+    memset(&a, 0, sizeof(a));
+    a.n = n;
+    a.ns = g.ns;
+    a.p_lo = g.p_lo;
+    a.p_hi = g.p_hi;
+    a.nitems = (npref + 31) / 32;
+    a.ctr = (Counters *)(base + L.ctr);
+    a.trace_idx = (unsigned long long *)idx_dev;
+    a.trace_val = (long long *)val_dev;
+    const Plan *plan = (const Plan *)(base + L.plan);
+    QBF_CUDA(launch_walk(kModeTrace, g.R, plan, (const Rec *)(base + L.recs), a,
+                         walk_grid(g.R, kModeTrace, n, g.ns, a.nitems), s),
+             "walk (trace)");
+    char *h = (char *)P->host;
+    QBF_CUDA(cudaMemcpyAsync(h, plan, offsetof(Plan, lin), cudaMemcpyDeviceToHost, s), "copy plan");
+    QBF_CUDA(cudaStreamSynchronize(s), "trace");
+    const Plan *PH = (const Plan *)h;
+    if (PH->status != QBF_OK)
+        return set_err(PH->status, "prepare failed");
+    *sigma_out = PH->sigma;
+    return QBF_OK;
+}
+
+int qbf_alu_microbench(int op, double *ops_per_clk_sm, double *sm_mhz, double *seconds,
+                       void *stream)
+{
+    if (!ops_per_clk_sm || !sm_mhz || !seconds)
+        return set_err(QBF_EINVAL, "null pointer argument");
+    if (op < 0 || op > 9)
+        return set_err(QBF_EINVAL, "op must be in [0, 9]");
+    std::lock_guard<std::mutex> lk(g_mu);
+    cudaError_t e = run_alu_microbench(op, ops_per_clk_sm, sm_mhz, seconds, (cudaStream_t)stream);
+    if (e != cudaSuccess)
+        return cuda_err(e, "alu microbench");
+    return QBF_OK;
+}
+
+const char *qbf_last_error_string(void) { return g_err.c_str(); }
+
+int qbf_release(void)
+{
+    std::lock_guard<std::mutex> lk(g_mu);
+    int cur = 0;
+    cudaGetDevice(&cur);
+    for (size_t d = 0; d < g_pools.size(); ++d) {
+        Pool &P = g_pools[d];
+        if (!P.dev && !P.host)
+            continue;
+        cudaSetDevice((int)d);
+        cudaDeviceSynchronize();
+        if (P.dev)
+            cudaFree(P.dev);
+        if (P.host)
+            cudaFreeHost(P.host);
+        P = Pool();
+    }
+    cudaSetDevice(cur);
+    return QBF_OK;
+}
+
+int qbf_version(void) { return 100; }
+
+}  // extern "C"

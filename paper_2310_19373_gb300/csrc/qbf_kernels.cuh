@@ -1,0 +1,61 @@
+// qbf_kernels.cuh -- launch interfaces between the host runtime and the kernels.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include "qbf_internal.cuh"
+
+namespace qbf {
+
+constexpr int kWalkThreads = 256;
+constexpr int kModeMin = 0;
+constexpr int kModeEmit = 1;
+constexpr int kModeTrace = 2;
+constexpr unsigned long long kCandCap = 1ull << 22;  // candidate states per solve
+
+struct WalkArgs {
+    int n;                          // variables
+    int ns;                         // suffix bits walked per thread
+    unsigned long long p_lo, p_hi;  // MIN/TRACE: prefixes [p_lo, p_hi)
+    unsigned long long nitems;      // MIN/TRACE: warp items = ceil((p_hi - p_lo) / 32)
+    int q;                          // EMIT: sub-prefix bits per flagged prefix
+    int lowest_mode;                // EMIT: walk only the lowest flagged prefix
+    const unsigned int *flagged;    // EMIT: flagged prefixes (absolute, n - ns - q bits)
+    Counters *ctr;
+    int *pmin;                      // MIN: per-prefix minimum, index p - p_lo
+    unsigned long long *cand;       // EMIT: candidate natural indices
+    unsigned long long cand_cap;
+    unsigned long long *trace_idx;  // TRACE
+    long long *trace_val;
+};
+
+// qbf_prepare.cu
+__global__ void prepare_kernel(const void *Q, int n, int dtype, Plan *plan);
+__global__ void tables_kernel(const Plan *plan, int ns, int R, Rec *recs, unsigned nrec, int *Kbuf);
+
+// qbf_walk.cu
+size_t walk_smem_bytes(int n, int ns, int R);
+int walk_blocks_per_sm(int R, int mode, size_t smem);
+cudaError_t launch_walk(int mode, int R, const Plan *plan, const Rec *recs, const WalkArgs &a,
+                        int grid, cudaStream_t s);
+cudaError_t copy_corrections(const int *Kbuf_dev, cudaStream_t s);
+
+// qbf_select.cu
+__global__ void reset_counters_kernel(Counters *c);
+__global__ void threshold_kernel(const Plan *plan, const int *pmin, unsigned long long npref,
+                                 int top_k, Counters *c);
+__global__ void flag_kernel(const Plan *plan, const int *pmin, unsigned long long npref,
+                            unsigned long long p_lo, int lowest_mode, unsigned int *flagged,
+                            Counters *c);
+__global__ void rescore_kernel(const Plan *plan, const void *Q, int n, int dtype,
+                               const unsigned long long *cand, const Counters *c,
+                               unsigned long long cap, long long *vals);
+__global__ void select_kernel(const Plan *plan, const unsigned long long *cand,
+                              const long long *vals, const Counters *c, unsigned long long cap,
+                              int top_k, DevResult *res);
+
+// qbf_microbench.cu
+cudaError_t run_alu_microbench(int op, double *ops_per_clk_sm, double *sm_mhz, double *seconds,
+                               cudaStream_t s);
+
+}  // namespace qbf

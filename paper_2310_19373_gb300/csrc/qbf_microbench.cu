@@ -1,0 +1,171 @@
+// qbf_microbench.cu -- ALU throughput of the instruction classes the walk uses.
+//
+// The walk is bound by integer/float ALU issue, not by HBM, so its roofline
+// denominator is the number of lane operations an SM retires per clock.
+// Each kernel below runs 8 independent dependency chains per thread of one
+// instruction class, fills every SM with one wave of resident blocks, and
+// times itself with the SM cycle counter.  The result is scalar lane
+// operations per SM clock per SM (a packed f32x2 add counts as two).
+#include <cstdint>
+#include <vector>
+
+#include "qbf_kernels.cuh"
+
+namespace qbf {
+
+namespace {
+
+constexpr int kMbThreads = 512;
+constexpr int kRounds = 16;  // unrolled rounds per iteration, 8 chains each
+
+__device__ __forceinline__ float fmin3(float a, float b, float c)
+{
+    float r;
+    asm("min.f32 %0, %1, %2, %3;" : "=f"(r) : "f"(a), "f"(b), "f"(c));
+    return r;
+}
+
+__device__ __forceinline__ unsigned long long fadd2(unsigned long long a, unsigned long long b)
+{
+    unsigned long long r;
+    asm("add.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(a), "l"(b));
+    return r;
+}
+
+template <int OP>
+__global__ void __launch_bounds__(kMbThreads) alu_kernel(int iters, unsigned seed, unsigned *sink,
+                                                         long long *cycles)
+{
+    unsigned a[8], m[8];
+    float f[8], g[8];
+    unsigned long long p[8];
+    for (int j = 0; j < 8; ++j) {
+        a[j] = seed * (threadIdx.x + 1) + j * 7919u;
+        m[j] = a[j] ^ 0x5bd1e995u;
+        f[j] = (float)(a[j] & 0xffff) * 1e-3f;
+        g[j] = f[j] + 1.0f;
+        p[j] = ((unsigned long long)__float_as_uint(f[j]) << 32) | __float_as_uint(g[j]);
+    }
+    const float fs = (float)(seed & 0xff) * 1e-7f;
+    __syncthreads();
+    const long long t0 = clock64();
+    for (int it = 0; it < iters; ++it) {
+#pragma unroll
+        for (int r = 0; r < kRounds; ++r) {
+#pragma unroll
+            for (int j = 0; j < 8; ++j) {
+                const int j1 = (j + 1) & 7, j2 = (j + 2) & 7;
+                if constexpr (OP == 0) {
+                    a[j] = a[j] + a[j1] + seed;
+                } else if constexpr (OP == 1) {
+                    a[j] = (unsigned)min((int)a[j], (int)a[j1]);
+                } else if constexpr (OP == 2) {
+                    a[j] = (unsigned)__vimin3_s32((int)a[j], (int)a[j1], (int)a[j2]);
+                } else if constexpr (OP == 3) {
+                    f[j] = f[j] + f[j1];
+                } else if constexpr (OP == 4) {
+                    f[j] = fmaf(f[j], f[j1], fs);
+                } else if constexpr (OP == 5) {
+                    f[j] = fminf(f[j], f[j1]);
+                } else if constexpr (OP == 6) {
+                    f[j] = fmin3(f[j], f[j1], f[j2]);
+                } else if constexpr (OP == 7) {
+                    p[j] = fadd2(p[j], p[j1]);
+                } else if constexpr (OP == 8) {
+                    a[j] = a[j] + m[j1] + seed;
+                    m[j] = (unsigned)min((int)m[j], (int)a[j]);
+                } else {
+                    f[j] = f[j] + g[j1];
+                    g[j] = fminf(g[j], f[j]);
+                }
+            }
+        }
+    }
+    const long long t1 = clock64();
+    unsigned acc = 0;
+    for (int j = 0; j < 8; ++j)
+        acc ^= a[j] ^ m[j] ^ __float_as_uint(f[j]) ^ __float_as_uint(g[j]) ^ (unsigned)p[j] ^
+               (unsigned)(p[j] >> 32);
+    if (acc == 0x12345678u)
+        sink[0] = acc;
+    if (threadIdx.x == 0)
+        cycles[blockIdx.x] = t1 - t0;
+}
+
+template <int OP>
+cudaError_t run_op(int iters, double *ops_per_clk_sm, double *sm_mhz, double *seconds,
+                   cudaStream_t s)
+{
+    int dev = 0, nsm = 0, bps = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess)
+        return e;
+    if ((e = cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess)
+        return e;
+    if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, alu_kernel<OP>, kMbThreads, 0)) !=
+        cudaSuccess)
+        return e;
+    if (bps < 1)
+        bps = 1;
+    const int grid = nsm * bps;
+    unsigned *sink = nullptr;
+    long long *cyc = nullptr;
+    if ((e = cudaMalloc(&sink, sizeof(unsigned))) != cudaSuccess)
+        return e;
+    if ((e = cudaMalloc(&cyc, sizeof(long long) * grid)) != cudaSuccess) {
+        cudaFree(sink);
+        return e;
+    }
+    cudaEvent_t ev0, ev1;
+    cudaEventCreate(&ev0);
+    cudaEventCreate(&ev1);
+    alu_kernel<OP><<<grid, kMbThreads, 0, s>>>(8, 12345u, sink, cyc);  // warm-up
+    cudaEventRecord(ev0, s);
+    alu_kernel<OP><<<grid, kMbThreads, 0, s>>>(iters, 12345u, sink, cyc);
+    cudaEventRecord(ev1, s);
+    e = cudaEventSynchronize(ev1);
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, ev0, ev1);
+    std::vector<long long> h(grid);
+    if (e == cudaSuccess)
+        e = cudaMemcpy(h.data(), cyc, sizeof(long long) * grid, cudaMemcpyDeviceToHost);
+    cudaEventDestroy(ev0);
+    cudaEventDestroy(ev1);
+    cudaFree(sink);
+    cudaFree(cyc);
+    if (e != cudaSuccess)
+        return e;
+    double mean_cyc = 0;
+    for (long long c : h)
+        mean_cyc += (double)c;
+    mean_cyc /= grid;
+    const double ops_per_thread = (double)iters * kRounds * 8 * ((OP == 7 || OP >= 8) ? 2 : 1);
+    const double ops_per_sm = ops_per_thread * kMbThreads * bps;
+    *ops_per_clk_sm = ops_per_sm / mean_cyc;
+    *seconds = ms * 1e-3;
+    *sm_mhz = mean_cyc / (ms * 1e-3) * 1e-6;
+    return cudaSuccess;
+}
+
+}  // namespace
+
+cudaError_t run_alu_microbench(int op, double *ops_per_clk_sm, double *sm_mhz, double *seconds,
+                               cudaStream_t s)
+{
+    const int iters = 20000;
+    switch (op) {
+    case 0: return run_op<0>(iters, ops_per_clk_sm, sm_mhz, seconds, s);
+    case 1: return run_op<1>(iters, ops_per_clk_sm, sm_mhz, seconds, s);
+    case 2: return run_op<2>(iters, ops_per_clk_sm, sm_mhz, seconds, s);
+    case 3: return run_op<3>(iters, ops_per_clk_sm, sm_mhz, seconds, s);
+    case 4: return run_op<4>(iters, ops_per_clk_sm, sm_mhz, seconds, s);
+    case 5: return run_op<5>(iters, ops_per_clk_sm, sm_mhz, seconds, s);
+    case 6: return run_op<6>(iters, ops_per_clk_sm, sm_mhz, seconds, s);
+    case 7: return run_op<7>(iters, ops_per_clk_sm, sm_mhz, seconds, s);
+    case 8: return run_op<8>(iters, ops_per_clk_sm, sm_mhz, seconds, s);
+    case 9: return run_op<9>(iters, ops_per_clk_sm, sm_mhz, seconds, s);
+    default: return cudaErrorInvalidValue;
+    }
+}
+
+}  // namespace qbf

@@ -1,0 +1,255 @@
+// qbf_prepare.cu -- step A1 of a solve: fixed-point image of Q and walk tables.
+//
+// prepare_kernel  (one CTA)
+//   Reads the caller's Q (any dtype), rejects NaN/Inf, forms lin_i = Q_ii and
+//   the symmetrised off-diagonal S_ij = Q_ij + Q_ji (Section 3's split of Q
+//   into a linear part and a symmetric quadratic part), picks the largest
+//   scale 2^sigma with sum |round(.)| < 2^31 and writes the int32 image, the
+//   quantisation error bound and the certification window W to the Plan.
+//
+// tables_kernel
+//   Builds, for a walk with suffix width ns and R unrolled low bits, the
+//   lane-invariant record of every block transition B and the static
+//   in-block corrections K[parity][u] (derivation in qbf_walk.cu).
+#include <cfloat>
+#include <climits>
+#include <cmath>
+
+#include "qbf_internal.cuh"
+
+namespace qbf {
+
+namespace {
+
+__device__ double load_q(const void *Q, int dtype, int e)
+{
+    switch (dtype) {
+    case QBF_F64: return static_cast<const double *>(Q)[e];
+    case QBF_F32: return (double)static_cast<const float *>(Q)[e];
+    case QBF_I32: return (double)static_cast<const int32_t *>(Q)[e];
+    default: return (double)static_cast<const int16_t *>(Q)[e];
+    }
+}
+
+// Deterministic block sum (fixed tree) for doubles; blockDim.x must be 256.
+__device__ double block_sum_d(double x, double *red)
+{
+    int t = threadIdx.x;
+    red[t] = x;
+    __syncthreads();
+    for (int s = 128; s > 0; s >>= 1) {
+        if (t < s)
+            red[t] = red[t] + red[t + s];
+        __syncthreads();
+    }
+    double r = red[0];
+    __syncthreads();
+    return r;
+}
+
+__device__ long long block_sum_ll(long long x, long long *red)
+{
+    int t = threadIdx.x;
+    red[t] = x;
+    __syncthreads();
+    for (int s = 128; s > 0; s >>= 1) {
+        if (t < s)
+            red[t] += red[t + s];
+        __syncthreads();
+    }
+    long long r = red[0];
+    __syncthreads();
+    return r;
+}
+
+}  // namespace
+
+__global__ void __launch_bounds__(256) prepare_kernel(const void *Q, int n, int dtype, Plan *plan)
+{
+    __shared__ double sQ[kMaxN * kMaxN];
+    __shared__ double redd[256];
+    __shared__ long long redl[256];
+    const int t = threadIdx.x;
+    const int nn = n * n;
+    const bool is_int = (dtype == QBF_I32 || dtype == QBF_I16);
+
+    int bad = 0;
+    for (int e = t; e < nn; e += blockDim.x) {
+        double q = load_q(Q, dtype, e);
+        if (!isfinite(q))
+            bad = 1;
+        sQ[e] = q;
+    }
+    bad = __syncthreads_or(bad);
+    if (bad) {
+        if (t == 0) {
+            plan->n = n;
+            plan->status = QBF_ENONFINITE;
+        }
+        return;
+    }
+
+    // V_all = sum |Q_ij| (bounds the FP64 canonical sum); V_sym = sum |lin| + sum_{i<j} |S_ij|.
+    double va = 0.0, vs = 0.0;
+    for (int e = t; e < nn; e += blockDim.x) {
+        int i = e / n, j = e % n;
+        va += fabs(sQ[e]);
+        if (i == j)
+            vs += fabs(sQ[e]);
+        else if (i < j)
+            vs += fabs(sQ[e] + sQ[j * n + i]);
+    }
+    const double V_all = block_sum_d(va, redd);
+    const double V_sym = block_sum_d(vs, redd);
+
+    int sigma = 0;
+    if (!is_int && V_sym > 0.0) {
+        double room = (2147483647.0 - (double)nn) / V_sym;
+        sigma = ilogb(room);  // floor(log2(room))
+        if (sigma > 1000)
+            sigma = 1000;
+        if (sigma < -1000)
+            sigma = -1000;
+    }
+    // Shrink sigma until the int32 image provably cannot overflow.
+    long long vhat = 0;
+    for (int iter = 0; iter < 64; ++iter) {
+        long long part = 0;
+        for (int e = t; e < nn; e += blockDim.x) {
+            int i = e / n, j = e % n;
+            if (i > j)
+                continue;
+            double x = (i == j) ? sQ[e] : sQ[e] + sQ[j * n + i];
+            part += llabs(__double2ll_rn(ldexp(x, sigma)));
+        }
+        vhat = block_sum_ll(part, redl);
+        if (vhat <= (long long)INT_MAX || is_int)
+            break;
+        --sigma;
+    }
+    if (is_int && vhat > (long long)INT_MAX) {
+        if (t == 0) {
+            plan->n = n;
+            plan->status = QBF_ERANGE;
+            plan->vhat = vhat;
+        }
+        return;
+    }
+
+    // int32 image and the quantisation error bound (quanta).
+    double eq = 0.0;
+    for (int e = t; e < nn; e += blockDim.x) {
+        int i = e / n, j = e % n;
+        if (i == j) {
+            double y = ldexp(sQ[e], sigma);
+            long long r = __double2ll_rn(y);
+            plan->lin[i] = (int)r;
+            plan->S[e] = 0;
+            eq += fabs((double)r - y);
+        } else {
+            double y = ldexp(sQ[e] + sQ[j * n + i], sigma);
+            long long r = __double2ll_rn(y);
+            plan->S[e] = (int)r;
+            if (i < j)
+                eq += fabs((double)r - y);
+        }
+    }
+    eq = block_sum_d(eq, redd);
+
+    if (t == 0) {
+        plan->n = n;
+        plan->dtype = dtype;
+        plan->sigma = sigma;
+        plan->vhat = vhat;
+        long long W = 0;
+        double Eq = 0.0;
+        if (!is_int) {
+            const double u = 0x1p-53;
+            // S_ij = Q_ij + Q_ji is itself rounded for FP64 input.
+            Eq = eq * (1.0 + 0x1p-40) + (dtype == QBF_F64 ? ldexp(u * V_all, sigma) : 0.0);
+            // |FP64 canonical sum - exact f| <= gamma_N * V_all, N = n^2 additions.
+            const double N = (double)nn;
+            const double e64 = (N * u / (1.0 - N * u)) * V_all;
+            double w = 2.0 * (Eq + ldexp(e64, sigma)) * (1.0 + 0x1p-30);
+            if (w > 0.0)
+                W = (long long)ceil(w) + 1;
+            if (W > (long long)INT_MAX)
+                W = INT_MAX;
+        }
+        plan->eq_quanta = Eq;
+        plan->window = W;
+        plan->error_bound = ldexp((double)W * 0.5, -sigma);
+        plan->status = QBF_OK;
+    }
+}
+
+// Records and in-block corrections for a walk over suffix bits 0..ns-1 with
+// R low bits unrolled (M = ns - R mid bits, 2^M blocks).  Record B (1 <= B < 2^M)
+// describes the flip at the start of block B; entry 0 is unused.
+__global__ void tables_kernel(const Plan *__restrict__ plan, int ns, int R, Rec *recs,
+                              unsigned nrec, int *Kbuf)
+{
+    if (plan->status != QBF_OK)
+        return;
+    const int n = plan->n;
+    const int *S = plan->S;
+    const int *lin = plan->lin;
+    const unsigned B = blockIdx.x * blockDim.x + threadIdx.x;
+
+    if (B == 0) {
+        // K[pi][u]: static part of the delta at in-block step u of a block of parity pi.
+        for (int pi = 0; pi < 2; ++pi) {
+            Kbuf[pi * 64] = 0;
+            for (int u = 1; u < 64; ++u) {
+                int val = 0;
+                if (u < (1 << R)) {
+                    int l = __ffs(u) - 1;
+                    int gprev = (u - 1) ^ ((u - 1) >> 1);
+                    int gnow = u ^ (u >> 1);
+                    int nb = ((gnow >> l) & 1) ^ ((l == R - 1) ? pi : 0);
+                    unsigned corr = 0;
+                    for (int j = 0; j < R; ++j) {
+                        if (j == l)
+                            continue;
+                        int bit = (gprev >> j) & 1;
+                        int d = (j == R - 1 && pi) ? -bit : bit;
+                        corr += (unsigned)(d * S[l * n + j]);
+                    }
+                    val = (int)(nb ? corr : 0u - corr);
+                }
+                Kbuf[pi * 64 + u] = val;
+            }
+        }
+    }
+    if (B == 0 || B >= nrec)
+        return;
+
+    const int l = R + __ffs(B) - 1;        // flipped bit: R + CTZ(B)
+    const unsigned g = B ^ (B >> 1);       // mid bits of the Gray state in block B
+    const unsigned gprev = (B - 1) ^ ((B - 1) >> 1);
+    const int nb = (g >> (l - R)) & 1;     // new value of bit l
+    unsigned U = (unsigned)lin[l];
+    for (int j = R; j < ns; ++j)
+        if (j != l && ((gprev >> (j - R)) & 1))
+            U += (unsigned)S[l * n + j];
+    if (B & 1)  // the low bits end block B-1 at e_{R-1} when B-1 is even
+        U += (unsigned)S[l * n + (R - 1)];
+    Rec r;
+    r.T = (int)(nb ? U : 0u - U);
+    r.code = 2 * (l - R) + nb;
+    for (int i = 0; i < kRMax; ++i) {
+        unsigned w = 0;
+        if (i < R) {
+            unsigned s_il = (unsigned)S[i * n + l];
+            w = nb ? s_il : 0u - s_il;
+            if (i != R - 1) {
+                unsigned s_ir = (unsigned)S[i * n + (R - 1)];
+                w += (B & 1) ? s_ir : 0u - s_ir;
+            }
+        }
+        r.W[i] = (int)w;
+    }
+    recs[B] = r;
+}
+
+}  // namespace qbf

@@ -1,0 +1,75 @@
+"""CPU-side checks of the C ABI: the library builds, loads and exports every
+function that include/qbf.h declares, and the binding's structs match the
+header's layout.  No compute call is made (no GPU here)."""
+import ctypes
+import os
+import re
+import shutil
+
+import pytest
+
+from conftest import ROOT
+
+HEADER = os.path.join(ROOT, "include", "qbf.h")
+
+
+def declared_functions():
+    text = open(HEADER).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"\b(qbf_[a-z0-9_]+)\s*\(", text)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    if shutil.which("nvcc") is None and not os.path.exists("/usr/local/cuda/bin/nvcc"):
+        pytest.skip("nvcc not available")
+    from paper_2310_19373_gb300 import build
+
+    build.build()
+    from paper_2310_19373_gb300 import _binding
+
+    return _binding.lib()
+
+
+def test_every_declared_symbol_is_exported(lib):
+    names = declared_functions()
+    assert "qbf_solve" in names and "qbf_last_error_string" in names
+    for name in names:
+        assert hasattr(lib, name), name
+
+
+def test_binding_covers_header(lib):
+    from paper_2310_19373_gb300 import _binding
+
+    for name in declared_functions():
+        assert name in _binding._SIGS, name
+        assert callable(getattr(_binding, name)), name
+
+
+def test_struct_sizes_match_header():
+    from paper_2310_19373_gb300 import _binding
+
+    # qbf_options: 4 ints + uint64 + 8 ints; qbf_result: see include/qbf.h
+    assert ctypes.sizeof(_binding.QbfOptions) == 4 * 4 + 8 + 8 * 4
+    exp = 8 + 8 + 4 + 4 + 8 * 64 + 8 * 64 + 4 + 4 + 8 + 8 + 4 + 4 + 4 + 4 + 8 + 4 + 3 * 4
+    assert ctypes.sizeof(_binding.QbfResult) == exp
+
+
+def test_default_options_and_version(lib):
+    from paper_2310_19373_gb300 import _binding
+
+    o = _binding.qbf_default_options()
+    assert (o.top_k, o.variant, o.prefix_bits, o.fix_bits) == (1, 0, -1, 0)
+    assert _binding.qbf_version() >= 100
+
+
+def test_constants_match_header():
+    from paper_2310_19373_gb300 import _binding
+
+    text = open(HEADER).read()
+    for name in ("QBF_OK", "QBF_EINVAL", "QBF_ENONFINITE", "QBF_EDTYPE", "QBF_ECUDA",
+                 "QBF_EOVERFLOW", "QBF_ENOTIMPL", "QBF_ERANGE", "QBF_F64", "QBF_F32",
+                 "QBF_I32", "QBF_I16"):
+        m = re.search(rf"\b{name}\s*=\s*(\d+)", text)
+        assert m, name
+        assert getattr(_binding, name) == int(m.group(1)), name
