@@ -134,6 +134,35 @@ int qbf_solve_host(const void *Q_host, int n, int dtype, const qbf_options *opt,
                    qbf_result *out, void *stream);
 
 /*
+ * qbf_solve_noalloc -- qbf_solve without any memory allocation by the call.
+ *
+ * The paper has no counterpart: this is a deployment variant of qbf_solve for
+ * callers that cannot allocate GPU memory -- processes that reserve the whole
+ * device up front and hand memory out only through their own pool, plug-ins
+ * whose host application owns the GPU memory budget, and services that cannot
+ * accept the device-wide synchronisation cudaMalloc/cudaFree can cause.  The
+ * caller passes Q and the result struct; all scratch lives in one array of
+ * QBF_NOALLOC_SCRATCH_BYTES compiled into the library, which every GPU that
+ * loads the library holds until the process exits.  No cudaMalloc, cudaFree
+ * or other allocating routine is called.
+ *
+ * Same arguments, semantics and result as qbf_solve, with these limits:
+ * n <= QBF_NOALLOC_MAX_N, at most 2^16 prefixes (prefix_bits <= 16) and 2^20
+ * suffix states per thread, at most 2^16 states in the certification window
+ * (else QBF_EOVERFLOW).  Larger problems are rejected with QBF_EINVAL and a
+ * message naming the limit.  The first call on a device looks up the scratch
+ * array's device address (cudaGetSymbolAddress) with that device current; make
+ * that first call before any stream capture.  All calls share the array and
+ * each leaves its contents behind (every call resets what must start at zero);
+ * calls whose GPU work overlaps race -- including with a concurrent qbf_solve --
+ * so issue them from one thread at a time.  The call waits for `stream`.
+ */
+#define QBF_NOALLOC_SCRATCH_BYTES (3u << 20) /* 3 MiB per device */
+#define QBF_NOALLOC_MAX_N 36
+int qbf_solve_noalloc(const void *Q_dev, int n, int dtype, const qbf_options *opt,
+                      qbf_result *out, void *stream);
+
+/*
  * qbf_walk_trace -- debug walk that records every visited state.
  *
  * Runs the split walk with 2^prefix_bits threads over the whole space

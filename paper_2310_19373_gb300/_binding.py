@@ -75,6 +75,9 @@ _SIGS = {
                                  ctypes.POINTER(QbfResult), _VP]),
     "qbf_solve_host": (ctypes.c_int, [_VP, ctypes.c_int, ctypes.c_int,
                                       ctypes.POINTER(QbfOptions), ctypes.POINTER(QbfResult), _VP]),
+    "qbf_solve_noalloc": (ctypes.c_int, [_VP, ctypes.c_int, ctypes.c_int,
+                                         ctypes.POINTER(QbfOptions), ctypes.POINTER(QbfResult),
+                                         _VP]),
     "qbf_walk_trace": (ctypes.c_int, [_VP, ctypes.c_int, ctypes.c_int, ctypes.c_int, _VP, _VP,
                                       ctypes.POINTER(ctypes.c_int), _VP]),
     "qbf_alu_microbench": (ctypes.c_int, [ctypes.c_int, ctypes.POINTER(ctypes.c_double),
@@ -131,6 +134,17 @@ def qbf_solve_host(Q_host: int, n: int, dtype: int, opt: QbfOptions | None,
     rc = lib().qbf_solve_host(_VP(Q_host), n, dtype,
                               ctypes.byref(opt) if opt is not None else None,
                               ctypes.byref(out), _VP(stream or 0))
+    _check(rc)
+    return out
+
+
+def qbf_solve_noalloc(Q_dev: int, n: int, dtype: int, opt: QbfOptions | None,
+                      stream: int | None = None):
+    """qbf_solve on the library's fixed scratch: for callers that cannot allocate GPU memory."""
+    out = QbfResult()
+    rc = lib().qbf_solve_noalloc(_VP(Q_dev), n, dtype,
+                                 ctypes.byref(opt) if opt is not None else None,
+                                 ctypes.byref(out), _VP(stream or 0))
     _check(rc)
     return out
 

@@ -375,6 +375,12 @@ int solve_locked(const void *Q, bool host_q, int n, int dtype, const qbf_options
 
 }  // namespace
 
+namespace qbf {
+// Lets other translation units of the library report errors through
+// qbf_last_error_string().
+int record_error(int code, const char *msg) { return set_err(code, msg); }
+}  // namespace qbf
+
 extern "C" {
 
 void qbf_default_options(qbf_options *opt)

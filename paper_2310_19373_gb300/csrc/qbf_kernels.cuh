@@ -54,6 +54,9 @@ __global__ void select_kernel(const Plan *plan, const unsigned long long *cand,
                               const long long *vals, const Counters *c, unsigned long long cap,
                               int top_k, DevResult *res);
 
+// qbf_api.cu: report an error through qbf_last_error_string(); returns code
+int record_error(int code, const char *msg);
+
 // qbf_microbench.cu
 cudaError_t run_alu_microbench(int op, double *ops_per_clk_sm, double *sm_mhz, double *seconds,
                                cudaStream_t s);
