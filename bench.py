@@ -196,6 +196,52 @@ def run_alu_microbench():
                           "lane_ops_per_clk_per_sm": rate / (nsm * f * 1e6), "sm_mhz": f}))
 
 
+def run_variants(dev, flush):
+    """Other workloads of the path, timed with CUDA events (reported beside the headline)."""
+    import numpy as np
+    import torch
+
+    from paper_2310_19373_gb300 import _binding as qb
+    from paper_2310_19373_gb300 import inputs
+
+    out = {}
+    stream = torch.cuda.current_stream(dev)
+
+    def timed(fn, reps=3):
+        fn()
+        ts = []
+        for _ in range(reps):
+            flush.zero_()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            fn()
+            e1.record(stream)
+            e1.synchronize()
+            ts.append(e0.elapsed_time(e1) * 1e-3)
+        return statistics.median(ts)
+
+    # batched: 4096 instances, n ~ U{16..34}, half FP32 uniform[-1,1], half int16
+    Qs = [torch.from_numpy(np.ascontiguousarray(q)).to(dev) for q in inputs.config_batched()]
+    states = float(sum(2 ** q.shape[0] for q in Qs))
+    t = timed(lambda: qb.solve_batched(Qs))
+    out["batched_4096"] = {"workload": "4096 QUBOs, n ~ U{16..34}, half FP32 uniform[-1,1], "
+                                       "half int16 uniform{-50..50}, seed 0; one persistent walk "
+                                       "under a CUDA graph",
+                           "states": states, "seconds": t, "states_per_s": states / t}
+    # n = 32 int32 (dense), exact
+    Q32 = torch.from_numpy(inputs.config_n32_int(0)).to(dev)
+    t = timed(lambda: qb.solve(Q32))
+    out["n32_int32"] = {"workload": "n=32 int32 uniform[-100,100], seed 0, exact",
+                        "seconds": t, "states_per_s": 2.0 ** 32 / t}
+    # n = 20 FP64 top-8 (latency)
+    Q20 = torch.from_numpy(inputs.config_n20_f64(0)).to(dev)
+    t = timed(lambda: qb.solve(Q20, top_k=8), reps=10)
+    out["n20_f64_top8"] = {"workload": "n=20 FP64 uniform[-1,1], seed 0, top-8",
+                           "seconds": t, "states_per_s": 2.0 ** 20 / t}
+    return out
+
+
 def load_traffic():
     """DRAM traffic of the walk kernel from the committed ncu summary, if still current."""
     import hashlib
@@ -220,6 +266,8 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-variants", action="store_true",
+                    help="skip the batched / n=32 / n=20 lines reported beside the headline")
     ap.add_argument("--profile-n", type=int, default=0,
                     help="profiling target: two solves of an n-variable Gaussian FP32 instance, "
                          "no timing (for ncu)")
@@ -349,6 +397,8 @@ def main():
         "gpu_launches": launches,
         "clocks": clk,
     }
+    if rank == 0 and world == 1 and not args.no_variants:
+        line["variants"] = run_variants(dev, flush)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(Qnp)
     if rank == 0:

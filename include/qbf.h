@@ -41,6 +41,8 @@ extern "C" {
 
 #define QBF_MAX_N 48    /* largest n for qbf_solve                        */
 #define QBF_MAX_TOPK 64 /* largest top_k                                  */
+#define QBF_BATCH_MAX_N 34          /* largest n of one batched instance  */
+#define QBF_BATCH_MAX_COUNT 65536   /* most instances per batched call    */
 
 /* element type of Q */
 typedef enum {
@@ -81,7 +83,9 @@ typedef struct {
     uint64_t fix_value;
     int timing;         /* 1: time the main walk kernel with CUDA events on
                            `stream` and report it in qbf_result.walk_seconds */
-    int reserved[7];
+    int batch_suffix_bits; /* qbf_solve_batched: suffix bits walked per lane,
+                              6..16; 0 = the autotuned value (default 14)  */
+    int reserved[6];
 } qbf_options;
 
 typedef struct {
@@ -134,6 +138,42 @@ int qbf_solve_host(const void *Q_host, int n, int dtype, const qbf_options *opt,
                    qbf_result *out, void *stream);
 
 /*
+ * qbf_solve_batched -- minimum and lowest-index argmin of many independent QUBOs.
+ *
+ * Section 3.1's prefix split applied across instances: the prefixes of all
+ * instances form one queue of equal-cost work items that a single persistent
+ * kernel drains; the whole pipeline (prepare, walk, certification, rescoring,
+ * per-instance selection) is replayed as one CUDA graph, rebuilt only when the
+ * batch layout changes.
+ *
+ * Q_dev     : host array of `count` device pointers; Q_dev[i] holds n[i]*n[i]
+ *             elements of dtype[i], row-major.
+ * n, dtype  : host arrays of `count` entries; 1 <= n[i] <= QBF_BATCH_MAX_N.
+ * opt       : NULL or top_k = 1, fix_bits = 0; batch_suffix_bits selects the
+ *             per-lane suffix width (0 = autotuned, see qbf_tune_batched).
+ * min_value, argmin : host arrays of `count` entries (same meaning as
+ *             qbf_result.min_value / argmin).
+ * 1 <= count <= QBF_BATCH_MAX_COUNT.  Errors name the first failing instance.
+ * Certification is per instance, as in qbf_solve; QBF_EOVERFLOW if the whole
+ * batch has more than 2^20 states inside its windows.
+ */
+int qbf_solve_batched(const void *const *Q_dev, const int *n, const int *dtype, int count,
+                      const qbf_options *opt, double *min_value, uint64_t *argmin, void *stream);
+
+/*
+ * qbf_tune_batched -- picks the per-lane suffix width of qbf_solve_batched.
+ *
+ * Times qbf_solve_batched on the given batch for every suffix width in
+ * [6, 16] between lo_bits and hi_bits, keeps the fastest as this process's
+ * default for the current device and returns it in *best_bits (and its time
+ * in *best_seconds).  If the environment variable QBF_TUNE_CACHE names a file,
+ * a line "<device name> <SM count> <bits> <seconds>" is appended to it.
+ */
+int qbf_tune_batched(const void *const *Q_dev, const int *n, const int *dtype, int count,
+                     int lo_bits, int hi_bits, int *best_bits, double *best_seconds,
+                     void *stream);
+
+/*
  * qbf_solve_noalloc -- qbf_solve without any memory allocation by the call.
  *
  * The paper has no counterpart: this is a deployment variant of qbf_solve for
@@ -175,6 +215,20 @@ int qbf_solve_noalloc(const void *Q_dev, int n, int dtype, const qbf_options *op
  */
 int qbf_walk_trace(const void *Q_dev, int n, int dtype, int prefix_bits, uint64_t *idx_dev,
                    int64_t *val_dev, int *sigma_out, void *stream);
+
+/*
+ * qbf_prefix_minima -- the MIN walk alone, exposing its per-prefix minima.
+ *
+ * Runs the production MIN walk (the kernel that dominates qbf_solve) with
+ * 2^prefix_bits threads over the whole space and writes, for every prefix p
+ * (the top prefix_bits variables), the minimum over its 2^(n - prefix_bits)
+ * suffix states of the fixed-point objective round(Q * 2^sigma) to
+ * pmin_dev[p] (int32, 2^prefix_bits entries, caller-owned device memory).
+ * *sigma_out receives sigma.  1 <= n <= 48, 0 <= prefix_bits <= min(n-1, 28).
+ * Used to test the walk prefix by prefix against the oracle.
+ */
+int qbf_prefix_minima(const void *Q_dev, int n, int dtype, int prefix_bits, int32_t *pmin_dev,
+                      int *sigma_out, void *stream);
 
 /*
  * qbf_alu_microbench -- measures one ALU instruction class on every SM.

@@ -36,7 +36,8 @@ class QbfOptions(ctypes.Structure):
         ("fix_bits", ctypes.c_int),
         ("fix_value", ctypes.c_uint64),
         ("timing", ctypes.c_int),
-        ("reserved", ctypes.c_int * 7),
+        ("batch_suffix_bits", ctypes.c_int),
+        ("reserved", ctypes.c_int * 6),
     ]
 
 
@@ -75,11 +76,21 @@ _SIGS = {
                                  ctypes.POINTER(QbfResult), _VP]),
     "qbf_solve_host": (ctypes.c_int, [_VP, ctypes.c_int, ctypes.c_int,
                                       ctypes.POINTER(QbfOptions), ctypes.POINTER(QbfResult), _VP]),
+    "qbf_solve_batched": (ctypes.c_int, [ctypes.POINTER(ctypes.c_void_p), ctypes.POINTER(ctypes.c_int),
+                                         ctypes.POINTER(ctypes.c_int), ctypes.c_int,
+                                         ctypes.POINTER(QbfOptions), ctypes.POINTER(ctypes.c_double),
+                                         ctypes.POINTER(ctypes.c_uint64), _VP]),
+    "qbf_tune_batched": (ctypes.c_int, [ctypes.POINTER(ctypes.c_void_p), ctypes.POINTER(ctypes.c_int),
+                                        ctypes.POINTER(ctypes.c_int), ctypes.c_int, ctypes.c_int,
+                                        ctypes.c_int, ctypes.POINTER(ctypes.c_int),
+                                        ctypes.POINTER(ctypes.c_double), _VP]),
     "qbf_solve_noalloc": (ctypes.c_int, [_VP, ctypes.c_int, ctypes.c_int,
                                          ctypes.POINTER(QbfOptions), ctypes.POINTER(QbfResult),
                                          _VP]),
     "qbf_walk_trace": (ctypes.c_int, [_VP, ctypes.c_int, ctypes.c_int, ctypes.c_int, _VP, _VP,
                                       ctypes.POINTER(ctypes.c_int), _VP]),
+    "qbf_prefix_minima": (ctypes.c_int, [_VP, ctypes.c_int, ctypes.c_int, ctypes.c_int, _VP,
+                                         ctypes.POINTER(ctypes.c_int), _VP]),
     "qbf_alu_microbench": (ctypes.c_int, [ctypes.c_int, ctypes.POINTER(ctypes.c_double),
                                           ctypes.POINTER(ctypes.c_double),
                                           ctypes.POINTER(ctypes.c_double), _VP]),
@@ -138,6 +149,48 @@ def qbf_solve_host(Q_host: int, n: int, dtype: int, opt: QbfOptions | None,
     return out
 
 
+def _batch_arrays(Q_ptrs, ns, dtypes):
+    count = len(Q_ptrs)
+    P = (ctypes.c_void_p * count)(*[ctypes.c_void_p(int(q)) for q in Q_ptrs])
+    N = (ctypes.c_int * count)(*[int(v) for v in ns])
+    D = (ctypes.c_int * count)(*[int(v) for v in dtypes])
+    return count, P, N, D
+
+
+def qbf_solve_batched(Q_ptrs, ns, dtypes, opt: QbfOptions | None, stream: int | None = None):
+    """Q_ptrs: device pointers; returns (min_values, argmins) as lists."""
+    count, P, N, D = _batch_arrays(Q_ptrs, ns, dtypes)
+    vmin = (ctypes.c_double * count)()
+    am = (ctypes.c_uint64 * count)()
+    rc = lib().qbf_solve_batched(P, N, D, count, ctypes.byref(opt) if opt is not None else None,
+                                 vmin, am, _VP(stream or 0))
+    _check(rc)
+    return list(vmin), [int(v) for v in am]
+
+
+def qbf_tune_batched(Q_ptrs, ns, dtypes, lo_bits: int = 6, hi_bits: int = 16,
+                     stream: int | None = None):
+    count, P, N, D = _batch_arrays(Q_ptrs, ns, dtypes)
+    best = ctypes.c_int()
+    sec = ctypes.c_double()
+    rc = lib().qbf_tune_batched(P, N, D, count, lo_bits, hi_bits, ctypes.byref(best),
+                                ctypes.byref(sec), _VP(stream or 0))
+    _check(rc)
+    return best.value, sec.value
+
+
+def solve_batched(Qs, batch_suffix_bits: int = 0, stream=None):
+    """Minimise a list of square CUDA tensors; returns (min_values, argmins)."""
+    import torch
+
+    Qs = [q.contiguous() for q in Qs]
+    opt = qbf_default_options()
+    opt.batch_suffix_bits = batch_suffix_bits
+    s = stream if stream is not None else torch.cuda.current_stream().cuda_stream
+    return qbf_solve_batched([q.data_ptr() for q in Qs], [q.shape[0] for q in Qs],
+                             [dtype_code(q) for q in Qs], opt, s)
+
+
 def qbf_solve_noalloc(Q_dev: int, n: int, dtype: int, opt: QbfOptions | None,
                       stream: int | None = None):
     """qbf_solve on the library's fixed scratch: for callers that cannot allocate GPU memory."""
@@ -154,6 +207,15 @@ def qbf_walk_trace(Q_dev: int, n: int, dtype: int, prefix_bits: int, idx_dev: in
     sigma = ctypes.c_int()
     rc = lib().qbf_walk_trace(_VP(Q_dev), n, dtype, prefix_bits, _VP(idx_dev), _VP(val_dev),
                               ctypes.byref(sigma), _VP(stream or 0))
+    _check(rc)
+    return sigma.value
+
+
+def qbf_prefix_minima(Q_dev: int, n: int, dtype: int, prefix_bits: int, pmin_dev: int,
+                      stream: int | None = None) -> int:
+    sigma = ctypes.c_int()
+    rc = lib().qbf_prefix_minima(_VP(Q_dev), n, dtype, prefix_bits, _VP(pmin_dev),
+                                 ctypes.byref(sigma), _VP(stream or 0))
     _check(rc)
     return sigma.value
 
@@ -252,6 +314,18 @@ def solve(Q, top_k: int = 1, variant: int = QBF_VARIANT_AUTO, prefix_bits: int =
         s = stream if stream is not None else torch.cuda.current_stream().cuda_stream
         r = qbf_solve_host(Q.data_ptr(), n, dtype_code(Q), opt, s)
     return _solution(r)
+
+
+def prefix_minima(Q, prefix_bits: int):
+    """Per-prefix minima of the fixed-point objective from the MIN walk, and sigma."""
+    import torch
+
+    Q = Q.contiguous()
+    n = Q.shape[0]
+    pm = torch.empty(1 << prefix_bits, dtype=torch.int32, device=Q.device)
+    s = torch.cuda.current_stream(Q.device).cuda_stream
+    sigma = qbf_prefix_minima(Q.data_ptr(), n, dtype_code(Q), prefix_bits, pm.data_ptr(), s)
+    return pm, sigma
 
 
 def walk_trace(Q, prefix_bits: int):

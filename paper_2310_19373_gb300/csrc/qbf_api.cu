@@ -17,6 +17,7 @@
 
 #include <algorithm>
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <mutex>
 #include <string>
@@ -77,7 +78,7 @@ Layout make_layout(size_t nrec, size_t npref, size_t qbytes, bool need_cand)
     L.res = o;
     o = align256(o + sizeof(DevResult));
     L.kbuf = o;
-    o = align256(o + sizeof(int) * 128);
+    o = align256(o + sizeof(int) * kKbufInts);
     L.recs = o;
     o = align256(o + sizeof(Rec) * std::max<size_t>(nrec, 2));
     L.pmin = o;
@@ -301,25 +302,25 @@ int solve_locked(const void *Q, bool host_q, int n, int dtype, const qbf_options
     threshold_kernel<<<1, 1024, 0, s>>>(plan, pmin, npref, o.top_k, ctr);
     QBF_CUDA(cudaGetLastError(), "threshold_kernel");
     const bool is_int = (dtype == QBF_I32 || dtype == QBF_I16);
-    // With W = 0 (integer Q) and top_k = 1 the lowest flagged prefix holds the
-    // answer; float Q with an all-zero image also has W = 0 and is exact.
-    const int lowest_mode = (o.top_k == 1 && is_int) ? 1 : 0;
+    // With exact values (W = 0: integer Q, or an all-zero float Q) and
+    // top_k = 1 the kernels re-walk only the lowest flagged prefix; they read
+    // W from the plan, so the host sizes the grid for the general case.
     {
         const int fb = (int)std::min<unsigned long long>((npref + 255) / 256, 4096);
-        flag_kernel<<<fb, 256, 0, s>>>(plan, pmin, npref, g.p_lo, lowest_mode, flagged, ctr);
+        flag_kernel<<<fb, 256, 0, s>>>(plan, pmin, npref, g.p_lo, o.top_k, flagged, ctr);
         QBF_CUDA(cudaGetLastError(), "flag_kernel");
     }
     WalkArgs e = a;
     e.ns = g.ns - g.q;
     e.q = g.q;
-    e.lowest_mode = lowest_mode;
+    e.top_k = o.top_k;
     e.flagged = flagged;
     e.cand = cand;
     e.cand_cap = kCandCap;
     e.pmin = nullptr;
     // the number of flagged prefixes is only known on the device: size the
     // persistent grid for the worst case, idle warps exit at once
-    const unsigned long long max_items = ((lowest_mode ? 1ull : npref) << g.q) / 32 + 1;
+    const unsigned long long max_items = (npref << g.q) / 32 + 1;
     QBF_CUDA(launch_walk(kModeEmit, g.R, plan, recs, e, walk_grid(g.R, kModeEmit, n, e.ns, max_items), s),
              "walk (emit)");
     rescore_kernel<<<256, 256, 0, s>>>(plan, Qdev, n, dtype, cand, ctr, kCandCap, vals);
@@ -457,6 +458,56 @@ int qbf_walk_trace(const void *Q_dev, int n, int dtype, int prefix_bits, uint64_
     return QBF_OK;
 }
 
+int qbf_prefix_minima(const void *Q_dev, int n, int dtype, int prefix_bits, int32_t *pmin_dev,
+                      int *sigma_out, void *stream)
+{
+    std::lock_guard<std::mutex> lk(g_mu);
+    cudaStream_t s = (cudaStream_t)stream;
+    if (!Q_dev || !pmin_dev || !sigma_out)
+        return set_err(QBF_EINVAL, "null pointer argument");
+    if (n < 1 || n > QBF_MAX_N)
+        return set_err(QBF_EINVAL, "n must be in [1, 48]");
+    if (dtype_size(dtype) == 0)
+        return set_err(QBF_EDTYPE, "unknown dtype");
+    if (prefix_bits < 0)
+        return set_err(QBF_EINVAL, "prefix_bits must be given");
+    qbf_options o;
+    qbf_default_options(&o);
+    o.prefix_bits = prefix_bits;
+    Geo g;
+    int rc = plan_geometry(n, o, &g);
+    if (rc)
+        return rc;
+    const Layout L = make_layout(1u << g.M, 0, 0, false);
+    Pool *P = nullptr;
+    if ((rc = pool_get(L.total, sizeof(DevResult) + sizeof(Plan), &P)))
+        return rc;
+    char *base = (char *)P->dev;
+    if ((rc = enqueue_prepare(Q_dev, n, dtype, g, base, L, s)))
+        return rc;
+    WalkArgs a;
+    memset(&a, 0, sizeof(a));
+    a.n = n;
+    a.ns = g.ns;
+    a.p_lo = g.p_lo;
+    a.p_hi = g.p_hi;
+    a.nitems = (g.p_hi - g.p_lo + 31) / 32;
+    a.ctr = (Counters *)(base + L.ctr);
+    a.pmin = pmin_dev;
+    const Plan *plan = (const Plan *)(base + L.plan);
+    QBF_CUDA(launch_walk(kModeMin, g.R, plan, (const Rec *)(base + L.recs), a,
+                         walk_grid(g.R, kModeMin, n, g.ns, a.nitems), s),
+             "walk (min)");
+    char *h = (char *)P->host;
+    QBF_CUDA(cudaMemcpyAsync(h, plan, offsetof(Plan, lin), cudaMemcpyDeviceToHost, s), "copy plan");
+    QBF_CUDA(cudaStreamSynchronize(s), "prefix minima");
+    const Plan *PH = (const Plan *)h;
+    if (PH->status != QBF_OK)
+        return set_err(PH->status, "prepare failed");
+    *sigma_out = PH->sigma;
+    return QBF_OK;
+}
+
 int qbf_alu_microbench(int op, double *ops_per_clk_sm, double *sm_mhz, double *seconds,
                        void *stream)
 {
@@ -471,10 +522,80 @@ int qbf_alu_microbench(int op, double *ops_per_clk_sm, double *sm_mhz, double *s
     return QBF_OK;
 }
 
+int qbf_solve_batched(const void *const *Q_dev, const int *n, const int *dtype, int count,
+                      const qbf_options *opt, double *min_value, uint64_t *argmin, void *stream)
+{
+    return solve_batched(Q_dev, n, dtype, count, opt, min_value, argmin, (cudaStream_t)stream,
+                         nullptr);
+}
+
+int qbf_tune_batched(const void *const *Q_dev, const int *n, const int *dtype, int count,
+                     int lo_bits, int hi_bits, int *best_bits, double *best_seconds, void *stream)
+{
+    if (!best_bits || !best_seconds)
+        return set_err(QBF_EINVAL, "null pointer argument");
+    lo_bits = std::max(lo_bits, kRMax);
+    hi_bits = std::min(hi_bits, 16);
+    if (lo_bits > hi_bits)
+        return set_err(QBF_EINVAL, "empty suffix-width range (valid: 6..16)");
+    cudaStream_t s = (cudaStream_t)stream;
+    std::vector<double> vmin(count);
+    std::vector<uint64_t> am(count);
+    int best = -1;
+    double best_t = 1e300;
+    for (int b = lo_bits; b <= hi_bits; ++b) {
+        qbf_options o;
+        qbf_default_options(&o);
+        o.batch_suffix_bits = b;
+        int rc = solve_batched(Q_dev, n, dtype, count, &o, vmin.data(), am.data(), s, nullptr);
+        if (rc)
+            return rc;
+        cudaEvent_t e0, e1;
+        QBF_CUDA(cudaEventCreate(&e0), "cudaEventCreate");
+        QBF_CUDA(cudaEventCreate(&e1), "cudaEventCreate");
+        QBF_CUDA(cudaEventRecord(e0, s), "cudaEventRecord");
+        rc = solve_batched(Q_dev, n, dtype, count, &o, vmin.data(), am.data(), s, nullptr);
+        QBF_CUDA(cudaEventRecord(e1, s), "cudaEventRecord");
+        QBF_CUDA(cudaEventSynchronize(e1), "cudaEventSynchronize");
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, e0, e1);
+        cudaEventDestroy(e0);
+        cudaEventDestroy(e1);
+        if (rc)
+            return rc;
+        if (ms * 1e-3 < best_t) {
+            best_t = ms * 1e-3;
+            best = b;
+        }
+    }
+    *best_bits = best;
+    *best_seconds = best_t;
+    int rc = set_tuned_batch_ns(best);
+    if (rc)
+        return rc;
+    if (const char *path = getenv("QBF_TUNE_CACHE")) {
+        int dev = 0, nsm = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+        cudaDeviceProp prop;
+        memset(&prop, 0, sizeof(prop));
+        cudaGetDeviceProperties(&prop, dev);
+        if (FILE *f = fopen(path, "a")) {
+            for (char *c = prop.name; *c; ++c)
+                if (*c == ' ')
+                    *c = '_';
+            fprintf(f, "%s %d %d %.6f\n", prop.name, nsm, best, best_t);
+            fclose(f);
+        }
+    }
+    return QBF_OK;
+}
+
 const char *qbf_last_error_string(void) { return g_err.c_str(); }
 
 int qbf_release(void)
 {
+    release_batched();
     std::lock_guard<std::mutex> lk(g_mu);
     int cur = 0;
     cudaGetDevice(&cur);

@@ -1,0 +1,691 @@
+// qbf_batched.cu -- many independent QUBOs of uneven n in one persistent pass.
+//
+// Work split (Section 3.1, applied across instances).  Instance i is walked
+// with ns_i suffix bits per lane and 2^(n_i - ns_i) prefixes; prefixes are
+// grouped into work items of 32 (one warp), and the items of all instances form
+// one global queue.  A persistent grid of 4-warp CTAs pulls items with an
+// atomic counter; each warp keeps the current instance's int32 image (S, lin)
+// and its in-block corrections in its own slice of shared memory and reloads
+// them only when it moves to another instance.  ns_i is the same for all large
+// instances, so items cost about the same and the tail is one item.
+//
+// Certification per instance is the single-instance rule (qbf_select.cu):
+// every item whose minimum is within W_i of instance i's minimum is re-walked,
+// its states <= gmin_i + W_i become candidates (instance, natural index), each
+// candidate is rescored in FP64 canonical order (float Q) or exact int64, and
+// the per-instance lexicographic minimum (value, index) is found with two
+// order-preserving 64-bit atomicMin passes (value first, then index among the
+// states with that value), so the answer does not depend on emission order.
+//
+// The whole sequence -- descriptor upload, reset, prepare, tables, MIN walk,
+// flags, EMIT walk, rescoring, argmin, result download -- is captured once in a
+// CUDA graph per batch layout and replayed.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <climits>
+#include <cstring>
+#include <mutex>
+#include <string>
+#include <vector>
+
+#include "qbf.h"
+#include "qbf_internal.cuh"
+#include "qbf_kernels.cuh"
+#include "qbf_walk_core.cuh"
+
+namespace qbf {
+
+namespace {
+
+constexpr int kBatchThreads = 128;
+constexpr int kBatchWarps = kBatchThreads / 32;
+constexpr int kBatchR = kRMax;
+constexpr int kBatchMaxNS = 16;
+constexpr int kBatchMinN = 11;  // smallest walk dimension: ns >= R and 32 prefixes per item
+constexpr int kWarpSmemInts =
+    QBF_BATCH_MAX_N * QBF_BATCH_MAX_N + QBF_BATCH_MAX_N + 128 + 2 * (kBatchMaxNS - kBatchR) * 32;
+constexpr unsigned long long kBatchCandCap = 1ull << 20;
+
+struct BatchArgs {
+    const BatchDesc *desc;
+    int count;
+    const Plan *plans;
+    const Rec *recs;
+    const int *K;
+    unsigned long long total_items;
+    int *item_min;
+    int *gmin;
+    const unsigned *flagged;
+    Counters *ctr;
+    unsigned long long *cand_idx;
+    unsigned *cand_inst;
+    unsigned long long cap;
+};
+
+__device__ __forceinline__ void emit_candidate(const BatchArgs &a, unsigned long long idx, int inst)
+{
+    const unsigned long long pos = atomicAdd(&a.ctr->cand, 1ull);
+    if (pos < a.cap) {
+        a.cand_idx[pos] = idx;
+        a.cand_inst[pos] = (unsigned)inst;
+    }
+}
+
+__device__ __forceinline__ int find_instance(const BatchDesc *d, int count, unsigned long long g)
+{
+    int lo = 0, hi = count - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (d[mid].item_off <= g)
+            lo = mid;
+        else
+            hi = mid - 1;
+    }
+    return lo;
+}
+
+template <int MODE>
+__global__ void __launch_bounds__(kBatchThreads) batched_walk_kernel(BatchArgs a)
+{
+    __shared__ int sm[kBatchWarps][kWarpSmemInts];
+    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    int *sS = sm[w];
+    int *sLin = sS, *sK = sS, *sC = sS;
+    int cur = -1, n = 0, ns = 0, tau = 0, ok = 0, exact = 0;
+    unsigned long long nprefix = 0, item_off = 0;
+    const int4 *rec4 = nullptr;
+    const unsigned long long total =
+        (MODE == kModeMin) ? a.total_items : (unsigned long long)a.ctr->flagged;
+
+    while (true) {
+        unsigned long long g = 0;
+        if (lane == 0)
+            g = atomicAdd(&a.ctr->items[MODE], 1ull);
+        g = __shfl_sync(0xffffffffu, g, 0);
+        if (g >= total)
+            break;
+        const unsigned long long gi = (MODE == kModeMin) ? g : (unsigned long long)a.flagged[g];
+        const int inst = find_instance(a.desc, a.count, gi);
+        if (inst != cur) {
+            __syncwarp();
+            const BatchDesc d = a.desc[inst];
+            const Plan *plan = a.plans + inst;
+            n = d.n;
+            ns = d.ns;
+            nprefix = d.nprefix;
+            item_off = d.item_off;
+            rec4 = reinterpret_cast<const int4 *>(a.recs + d.rec_off);
+            ok = (plan->status == QBF_OK);
+            sLin = sS + n * n;
+            sK = sLin + n;
+            sC = sK + 128;
+            for (int e = lane; e < n * n; e += 32)
+                sS[e] = plan->S[e];
+            for (int e = lane; e < n; e += 32)
+                sLin[e] = plan->lin[e];
+            for (int e = lane; e < 128; e += 32)
+                sK[e] = a.K[inst * 128 + e];
+            if (MODE == kModeEmit && ok) {
+                const long long t = (long long)a.gmin[inst] + plan->window;
+                tau = (int)(t > (long long)INT_MAX ? (long long)INT_MAX : t);
+                exact = (plan->window == 0);
+            }
+            cur = inst;
+            __syncwarp();
+        }
+        if (!ok)
+            continue;
+        const unsigned long long pl = (gi - item_off) * 32 + lane;
+        const bool active = pl < nprefix;
+        const unsigned long long p = active ? pl : 0;
+        unsigned GL[kBatchR];
+        const unsigned v = lane_setup<kBatchR>(p, n, ns, sS, sLin, sC, 32, lane, GL);
+        if constexpr (MODE == kModeMin) {
+            const int m = walk_suffix_min<kBatchR>(v, GL, ns, rec4, sC, 32, lane, SmemK{sK});
+            int wm = active ? m : INT_MAX;
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1)
+                wm = min(wm, __shfl_xor_sync(0xffffffffu, wm, o));
+            if (lane == 0) {
+                a.item_min[gi] = wm;
+                atomicMin(&a.gmin[inst], wm);
+            }
+        } else if (exact) {
+            // W = 0: the values are exact, so only the lowest tied index of
+            // each lane can win; emit that one state per lane
+            const unsigned long long pbase = p << ns;
+            unsigned long long best = ~0ull;
+            walk_suffix_visit<kBatchR>(v, GL, ns, rec4, sC, 32, lane, SmemK{sK},
+                                       [&](unsigned val, unsigned t) {
+                                           if ((int)val <= tau) {
+                                               const unsigned long long x =
+                                                   pbase | (unsigned long long)(t ^ (t >> 1));
+                                               best = x < best ? x : best;
+                                           }
+                                       });
+            if (active && best != ~0ull)
+                emit_candidate(a, best, inst);
+        } else {
+            const unsigned long long pbase = p << ns;
+            walk_suffix_visit<kBatchR>(v, GL, ns, rec4, sC, 32, lane, SmemK{sK},
+                                       [&](unsigned val, unsigned t) {
+                                           if ((int)val <= tau && active)
+                                               emit_candidate(
+                                                   a, pbase | (unsigned long long)(t ^ (t >> 1)),
+                                                   inst);
+                                       });
+        }
+    }
+}
+
+__global__ void batched_reset_kernel(int count, int *gmin, unsigned long long *best_key,
+                                     unsigned long long *best_idx, unsigned *lowest, Counters *ctr)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < count) {
+        gmin[i] = INT_MAX;
+        lowest[i] = 0xFFFFFFFFu;
+        best_key[i] = ~0ull;
+        best_idx[i] = ~0ull;
+    }
+    if (i == 0) {
+        ctr->gmin = INT_MAX;
+        ctr->tau = 0;
+        ctr->flagged = 0;
+        ctr->lowest = 0xFFFFFFFFu;
+        for (int j = 0; j < 4; ++j)
+            ctr->items[j] = 0;
+        ctr->cand = 0;
+        ctr->status = QBF_OK;
+    }
+}
+
+// Items that can hold a winning state.  With W = 0 (exact values) only the
+// lowest such item of an instance is kept: its lowest tied state has the
+// lowest natural index of the instance.
+__global__ void batched_flag_kernel(const BatchDesc *desc, int count, const Plan *plans,
+                                    const int *item_min, const int *gmin,
+                                    unsigned long long total_items, unsigned *flagged,
+                                    unsigned *lowest, Counters *ctr)
+{
+    for (unsigned long long g = blockIdx.x * (unsigned long long)blockDim.x + threadIdx.x;
+         g < total_items; g += (unsigned long long)gridDim.x * blockDim.x) {
+        const int inst = find_instance(desc, count, g);
+        const Plan *plan = plans + inst;
+        if (plan->status != QBF_OK)
+            continue;
+        const long long tau = (long long)gmin[inst] + plan->window;
+        if ((long long)item_min[g] <= tau) {
+            if (plan->window == 0)
+                atomicMin(&lowest[inst], (unsigned)g);
+            else
+                flagged[atomicAdd(&ctr->flagged, 1u)] = (unsigned)g;
+        }
+    }
+}
+
+__global__ void batched_lowest_kernel(int count, const unsigned *lowest, unsigned *flagged,
+                                      Counters *ctr)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < count && lowest[i] != 0xFFFFFFFFu)
+        flagged[atomicAdd(&ctr->flagged, 1u)] = lowest[i];
+}
+
+// order-preserving 64-bit keys
+__device__ __forceinline__ unsigned long long key_of_double(double v)
+{
+    if (v == 0.0)
+        v = 0.0;  // -0 and +0 compare equal
+    const unsigned long long b = (unsigned long long)__double_as_longlong(v);
+    return (b >> 63) ? ~b : (b | 0x8000000000000000ull);
+}
+
+__device__ __forceinline__ unsigned long long key_of_int(long long v)
+{
+    return (unsigned long long)v ^ 0x8000000000000000ull;
+}
+
+__device__ __forceinline__ double q_at_b(const void *Q, int dtype, int e)
+{
+    switch (dtype) {
+    case QBF_F64: return static_cast<const double *>(Q)[e];
+    case QBF_F32: return (double)static_cast<const float *>(Q)[e];
+    case QBF_I32: return (double)static_cast<const int32_t *>(Q)[e];
+    default: return (double)static_cast<const int16_t *>(Q)[e];
+    }
+}
+
+// FP64 canonical order (float Q) or exact int64 (integer Q) over the caller's
+// n_src variables; padded variables contribute exact zeros.
+__global__ void batched_rescore_kernel(const BatchDesc *desc, const unsigned long long *cand_idx,
+                                       const unsigned *cand_inst, const Counters *ctr,
+                                       unsigned long long cap, unsigned long long *keys,
+                                       unsigned long long *best_key)
+{
+    const unsigned long long count = ctr->cand < cap ? ctr->cand : cap;
+    for (unsigned long long e = blockIdx.x * (unsigned long long)blockDim.x + threadIdx.x;
+         e < count; e += (unsigned long long)gridDim.x * blockDim.x) {
+        const unsigned inst = cand_inst[e];
+        const BatchDesc d = desc[inst];
+        const unsigned long long x = cand_idx[e];
+        const int n = d.n_src;
+        unsigned long long key;
+        if (d.dtype == QBF_I32 || d.dtype == QBF_I16) {
+            long long acc = 0;
+            for (int i = 0; i < n; ++i) {
+                if (!((x >> i) & 1ull))
+                    continue;
+                long long row = (long long)q_at_b(d.Q, d.dtype, i * n + i);
+                for (int j = i + 1; j < n; ++j)
+                    if ((x >> j) & 1ull)
+                        row += (long long)q_at_b(d.Q, d.dtype, i * n + j) +
+                               (long long)q_at_b(d.Q, d.dtype, j * n + i);
+                acc += row;
+            }
+            key = key_of_int(acc);
+        } else {
+            double acc = 0.0;
+            for (int i = 0; i < n; ++i) {
+                if (!((x >> i) & 1ull))
+                    continue;
+                double row = q_at_b(d.Q, d.dtype, i * n + i);
+                for (int j = i + 1; j < n; ++j)
+                    if ((x >> j) & 1ull)
+                        row = __dadd_rn(row, __dadd_rn(q_at_b(d.Q, d.dtype, i * n + j),
+                                                       q_at_b(d.Q, d.dtype, j * n + i)));
+                acc = __dadd_rn(acc, row);
+            }
+            key = key_of_double(acc);
+        }
+        keys[e] = key;
+        atomicMin(&best_key[inst], key);
+    }
+}
+
+__global__ void batched_argmin_kernel(const unsigned long long *cand_idx,
+                                      const unsigned *cand_inst, const Counters *ctr,
+                                      unsigned long long cap, const unsigned long long *keys,
+                                      const unsigned long long *best_key,
+                                      unsigned long long *best_idx)
+{
+    const unsigned long long count = ctr->cand < cap ? ctr->cand : cap;
+    for (unsigned long long e = blockIdx.x * (unsigned long long)blockDim.x + threadIdx.x;
+         e < count; e += (unsigned long long)gridDim.x * blockDim.x) {
+        const unsigned inst = cand_inst[e];
+        if (keys[e] == best_key[inst])
+            atomicMin(&best_idx[inst], cand_idx[e]);
+    }
+}
+
+// ------------------------------------------------------------------------
+// host side
+
+struct BLayout {
+    size_t desc, plans, K, recs, item_min, flagged, gmin, best_key, best_idx, status, lowest,
+        ctr, cand_idx, cand_inst, keys, total;
+};
+
+size_t a256(size_t x) { return (x + 255) & ~(size_t)255; }
+
+BLayout blayout(int count, unsigned long long nrec, unsigned long long items)
+{
+    BLayout L;
+    size_t o = 0;
+    auto take = [&](size_t bytes) {
+        size_t at = o;
+        o = a256(o + bytes);
+        return at;
+    };
+    L.desc = take(sizeof(BatchDesc) * count);
+    L.plans = take(sizeof(Plan) * count);
+    L.K = take(sizeof(int) * 128 * count);
+    L.recs = take(sizeof(Rec) * nrec);
+    L.item_min = take(sizeof(int) * items);
+    L.flagged = take(sizeof(unsigned) * items);
+    L.gmin = take(sizeof(int) * count);
+    L.best_key = take(sizeof(unsigned long long) * count);
+    L.best_idx = take(sizeof(unsigned long long) * count);
+    L.status = take(sizeof(int) * count);
+    L.lowest = take(sizeof(unsigned) * count);
+    L.ctr = take(sizeof(Counters));
+    L.cand_idx = take(sizeof(unsigned long long) * kBatchCandCap);
+    L.cand_inst = take(sizeof(unsigned) * kBatchCandCap);
+    L.keys = take(sizeof(unsigned long long) * kBatchCandCap);
+    L.total = o;
+    return L;
+}
+
+// host staging (pinned): descriptors in, results out
+struct BStage {
+    size_t desc, best_key, best_idx, status, ctr, total;
+};
+
+BStage bstage(int count)
+{
+    BStage S;
+    size_t o = 0;
+    auto take = [&](size_t bytes) {
+        size_t at = o;
+        o = a256(o + bytes);
+        return at;
+    };
+    S.desc = take(sizeof(BatchDesc) * count);
+    S.best_key = take(sizeof(unsigned long long) * count);
+    S.best_idx = take(sizeof(unsigned long long) * count);
+    S.status = take(sizeof(int) * count);
+    S.ctr = take(sizeof(Counters));
+    S.total = o;
+    return S;
+}
+
+struct GraphKey {
+    int count;
+    int ns_max;
+    unsigned long long nrec, items;
+    void *dev, *host;
+    int grid_min, grid_emit;
+    bool operator==(const GraphKey &o) const { return memcmp(this, &o, sizeof(*this)) == 0; }
+};
+
+struct BatchState {
+    void *dev = nullptr;
+    size_t dev_bytes = 0;
+    void *host = nullptr;
+    size_t host_bytes = 0;
+    cudaStream_t cap_stream = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    GraphKey key;
+    bool have_key = false;
+    int tuned_ns = 0;
+};
+
+std::mutex g_bmu;
+std::vector<BatchState> g_bstate;
+
+int walk_bps(int mode)
+{
+    int b = 0;
+    cudaError_t e;
+    if (mode == kModeMin)
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, batched_walk_kernel<kModeMin>,
+                                                          kBatchThreads, 0);
+    else
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, batched_walk_kernel<kModeEmit>,
+                                                          kBatchThreads, 0);
+    return (e != cudaSuccess || b < 1) ? 1 : b;
+}
+
+#define B_CUDA(call, where)                                                                      \
+    do {                                                                                         \
+        cudaError_t b_e_ = (call);                                                               \
+        if (b_e_ != cudaSuccess)                                                                 \
+            return record_error(QBF_ECUDA, (std::string(where) + ": " + cudaGetErrorString(b_e_)).c_str()); \
+    } while (0)
+
+int enqueue_batch(BatchState &B, const BLayout &L, const BStage &S, int count,
+                  unsigned long long items, int grid_min, int grid_emit, cudaStream_t s)
+{
+    char *d = (char *)B.dev;
+    char *h = (char *)B.host;
+    const BatchDesc *desc = (const BatchDesc *)(d + L.desc);
+    Plan *plans = (Plan *)(d + L.plans);
+    int *K = (int *)(d + L.K);
+    Rec *recs = (Rec *)(d + L.recs);
+    Counters *ctr = (Counters *)(d + L.ctr);
+    int *gmin = (int *)(d + L.gmin);
+    unsigned long long *best_key = (unsigned long long *)(d + L.best_key);
+    unsigned long long *best_idx = (unsigned long long *)(d + L.best_idx);
+
+    B_CUDA(cudaMemcpyAsync(d + L.desc, h + S.desc, sizeof(BatchDesc) * count,
+                           cudaMemcpyHostToDevice, s),
+           "batch descriptors");
+    unsigned *lowest = (unsigned *)(d + L.lowest);
+    batched_reset_kernel<<<(count + 255) / 256, 256, 0, s>>>(count, gmin, best_key, best_idx,
+                                                             lowest, ctr);
+    batched_prepare_kernel<<<count, 256, 0, s>>>(desc, plans, (int *)(d + L.status));
+    batched_tables_kernel<<<count, 256, 0, s>>>(desc, plans, recs, K);
+    BatchArgs a;
+    memset(&a, 0, sizeof(a));
+    a.desc = desc;
+    a.count = count;
+    a.plans = plans;
+    a.recs = recs;
+    a.K = K;
+    a.total_items = items;
+    a.item_min = (int *)(d + L.item_min);
+    a.gmin = gmin;
+    a.flagged = (const unsigned *)(d + L.flagged);
+    a.ctr = ctr;
+    a.cand_idx = (unsigned long long *)(d + L.cand_idx);
+    a.cand_inst = (unsigned *)(d + L.cand_inst);
+    a.cap = kBatchCandCap;
+    batched_walk_kernel<kModeMin><<<grid_min, kBatchThreads, 0, s>>>(a);
+    const int fb = (int)std::min<unsigned long long>((items + 255) / 256, 8192);
+    batched_flag_kernel<<<fb, 256, 0, s>>>(desc, count, plans, a.item_min, gmin, items,
+                                           (unsigned *)(d + L.flagged), lowest, ctr);
+    batched_lowest_kernel<<<(count + 255) / 256, 256, 0, s>>>(count, lowest,
+                                                              (unsigned *)(d + L.flagged), ctr);
+    batched_walk_kernel<kModeEmit><<<grid_emit, kBatchThreads, 0, s>>>(a);
+    unsigned long long *keys = (unsigned long long *)(d + L.keys);
+    batched_rescore_kernel<<<512, 256, 0, s>>>(desc, a.cand_idx, a.cand_inst, ctr, kBatchCandCap,
+                                               keys, best_key);
+    batched_argmin_kernel<<<512, 256, 0, s>>>(a.cand_idx, a.cand_inst, ctr, kBatchCandCap, keys,
+                                              best_key, best_idx);
+    B_CUDA(cudaGetLastError(), "batched kernels");
+    B_CUDA(cudaMemcpyAsync(h + S.best_key, best_key, sizeof(unsigned long long) * count,
+                           cudaMemcpyDeviceToHost, s),
+           "batch results");
+    B_CUDA(cudaMemcpyAsync(h + S.best_idx, best_idx, sizeof(unsigned long long) * count,
+                           cudaMemcpyDeviceToHost, s),
+           "batch results");
+    B_CUDA(cudaMemcpyAsync(h + S.status, d + L.status, sizeof(int) * count, cudaMemcpyDeviceToHost,
+                           s),
+           "batch status");
+    B_CUDA(cudaMemcpyAsync(h + S.ctr, ctr, sizeof(Counters), cudaMemcpyDeviceToHost, s),
+           "batch counters");
+    return QBF_OK;
+}
+
+int dtsize(int dt)
+{
+    return dt == QBF_F64 ? 8 : (dt == QBF_F32 || dt == QBF_I32) ? 4 : dt == QBF_I16 ? 2 : 0;
+}
+
+}  // namespace
+
+int solve_batched(const void *const *Q, const int *n, const int *dtype, int count,
+                  const qbf_options *opt_in, double *min_value, uint64_t *argmin,
+                  cudaStream_t s, int *kernel_launches)
+{
+    if (!Q || !n || !dtype || !min_value || !argmin)
+        return record_error(QBF_EINVAL, "null pointer argument");
+    if (count < 1 || count > QBF_BATCH_MAX_COUNT)
+        return record_error(QBF_EINVAL, "count must be in [1, 65536]");
+    qbf_options o;
+    qbf_default_options(&o);
+    if (opt_in)
+        o = *opt_in;
+    if (o.top_k != 0 && o.top_k != 1)
+        return record_error(QBF_ENOTIMPL, "qbf_solve_batched returns the minimum only (top_k = 1)");
+    if (o.fix_bits != 0)
+        return record_error(QBF_ENOTIMPL, "qbf_solve_batched does not restrict the space");
+    std::lock_guard<std::mutex> lk(g_bmu);
+    int dev = 0;
+    B_CUDA(cudaGetDevice(&dev), "cudaGetDevice");
+    if ((int)g_bstate.size() <= dev)
+        g_bstate.resize(dev + 1);
+    BatchState &B = g_bstate[dev];
+    int NS = o.batch_suffix_bits > 0 ? o.batch_suffix_bits : (B.tuned_ns > 0 ? B.tuned_ns : 14);
+    if (NS < kBatchR || NS > kBatchMaxNS)
+        return record_error(QBF_EINVAL, "batch_suffix_bits must be in [6, 16]");
+
+    // plan every instance
+    std::vector<BatchDesc> desc(count);
+    unsigned long long items = 0, nrec = 0;
+    int ns_max = 0;
+    for (int i = 0; i < count; ++i) {
+        if (!Q[i])
+            return record_error(QBF_EINVAL, ("null Q for instance " + std::to_string(i)).c_str());
+        if (n[i] < 1 || n[i] > QBF_BATCH_MAX_N)
+            return record_error(QBF_EINVAL,
+                                ("instance " + std::to_string(i) + ": n must be in [1, 34]").c_str());
+        if (dtsize(dtype[i]) == 0)
+            return record_error(QBF_EDTYPE, ("instance " + std::to_string(i) + ": unknown dtype").c_str());
+        BatchDesc &d = desc[i];
+        d.Q = Q[i];
+        d.n_src = n[i];
+        d.n = std::max(n[i], kBatchMinN);
+        d.dtype = dtype[i];
+        d.ns = std::max(kBatchR, std::min(NS, d.n - 5));
+        d.nprefix = 1ull << (d.n - d.ns);
+        d.item_off = items;
+        d.rec_off = nrec;
+        items += (d.nprefix + 31) / 32;
+        nrec += 1ull << (d.ns - kBatchR);
+        ns_max = std::max(ns_max, d.ns);
+    }
+    const BLayout L = blayout(count, nrec, items);
+    const BStage S = bstage(count);
+    bool relayout = false;
+    if (B.dev_bytes < L.total) {
+        B_CUDA(cudaDeviceSynchronize(), "cudaDeviceSynchronize");
+        if (B.dev)
+            cudaFree(B.dev);
+        B.dev = nullptr;
+        B.dev_bytes = 0;
+        B_CUDA(cudaMalloc(&B.dev, L.total), "cudaMalloc(batch scratch)");
+        B.dev_bytes = L.total;
+        relayout = true;
+    }
+    if (B.host_bytes < S.total) {
+        B_CUDA(cudaDeviceSynchronize(), "cudaDeviceSynchronize");
+        if (B.host)
+            cudaFreeHost(B.host);
+        B.host = nullptr;
+        B.host_bytes = 0;
+        B_CUDA(cudaMallocHost(&B.host, S.total), "cudaMallocHost(batch staging)");
+        B.host_bytes = S.total;
+        relayout = true;
+    }
+    if (!B.cap_stream)
+        B_CUDA(cudaStreamCreateWithFlags(&B.cap_stream, cudaStreamNonBlocking), "capture stream");
+
+    int nsm = 1;
+    cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+    const int grid_min = (int)std::max<unsigned long long>(
+        1, std::min<unsigned long long>((unsigned long long)nsm * walk_bps(kModeMin),
+                                        (items + kBatchWarps - 1) / kBatchWarps));
+    const int grid_emit = nsm * walk_bps(kModeEmit);
+
+    char *h = (char *)B.host;
+    // the previous replay may still read the staging buffer: wait for it
+    B_CUDA(cudaStreamSynchronize(s), "batch stream");
+    memcpy(h + S.desc, desc.data(), sizeof(BatchDesc) * count);
+
+    GraphKey key;
+    memset(&key, 0, sizeof(key));
+    key.count = count;
+    key.ns_max = ns_max;
+    key.nrec = nrec;
+    key.items = items;
+    key.dev = B.dev;
+    key.host = B.host;
+    key.grid_min = grid_min;
+    key.grid_emit = grid_emit;
+    if (relayout || !B.have_key || !(B.key == key) || !B.exec) {
+        if (B.exec) {
+            cudaGraphExecDestroy(B.exec);
+            B.exec = nullptr;
+        }
+        cudaGraph_t graph = nullptr;
+        B_CUDA(cudaStreamBeginCapture(B.cap_stream, cudaStreamCaptureModeThreadLocal),
+               "begin capture");
+        int rc = enqueue_batch(B, L, S, count, items, grid_min, grid_emit, B.cap_stream);
+        cudaError_t ce = cudaStreamEndCapture(B.cap_stream, &graph);
+        if (rc)
+            return rc;
+        B_CUDA(ce, "end capture");
+        B_CUDA(cudaGraphInstantiate(&B.exec, graph, 0), "graph instantiate");
+        cudaGraphDestroy(graph);
+        B.key = key;
+        B.have_key = true;
+    }
+    B_CUDA(cudaGraphLaunch(B.exec, s), "graph launch");
+    B_CUDA(cudaStreamSynchronize(s), "batched solve");
+    if (kernel_launches)
+        *kernel_launches = 10;
+
+    const unsigned long long *bk = (const unsigned long long *)(h + S.best_key);
+    const unsigned long long *bi = (const unsigned long long *)(h + S.best_idx);
+    const int *st = (const int *)(h + S.status);
+    const Counters *ctr = (const Counters *)(h + S.ctr);
+    for (int i = 0; i < count; ++i) {
+        if (st[i] != QBF_OK)
+            return record_error(st[i], ("instance " + std::to_string(i) +
+                                        (st[i] == QBF_ENONFINITE ? ": Q holds NaN or Inf"
+                                                                 : ": integer Q too large"))
+                                           .c_str());
+    }
+    if (ctr->cand > kBatchCandCap)
+        return record_error(QBF_EOVERFLOW, "more than 2^20 candidate states in the batch");
+    for (int i = 0; i < count; ++i) {
+        const bool is_int = (dtype[i] == QBF_I32 || dtype[i] == QBF_I16);
+        const unsigned long long k = bk[i];
+        if (k == ~0ull || bi[i] == ~0ull)
+            return record_error(QBF_ECUDA, ("instance " + std::to_string(i) +
+                                            ": internal error, no candidate").c_str());
+        if (is_int) {
+            min_value[i] = (double)(long long)(k ^ 0x8000000000000000ull);
+        } else {
+            const unsigned long long b = (k >> 63) ? (k & 0x7FFFFFFFFFFFFFFFull) : ~k;
+            double v;
+            memcpy(&v, &b, sizeof(v));
+            min_value[i] = v;
+        }
+        argmin[i] = bi[i];
+    }
+    return QBF_OK;
+}
+
+int set_tuned_batch_ns(int ns)
+{
+    std::lock_guard<std::mutex> lk(g_bmu);
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess)
+        return record_error(QBF_ECUDA, "cudaGetDevice");
+    if ((int)g_bstate.size() <= dev)
+        g_bstate.resize(dev + 1);
+    g_bstate[dev].tuned_ns = ns;
+    return QBF_OK;
+}
+
+int release_batched()
+{
+    std::lock_guard<std::mutex> lk(g_bmu);
+    int cur = 0;
+    cudaGetDevice(&cur);
+    for (size_t d = 0; d < g_bstate.size(); ++d) {
+        BatchState &B = g_bstate[d];
+        if (!B.dev && !B.host && !B.exec && !B.cap_stream)
+            continue;
+        cudaSetDevice((int)d);
+        cudaDeviceSynchronize();
+        if (B.exec)
+            cudaGraphExecDestroy(B.exec);
+        if (B.cap_stream)
+            cudaStreamDestroy(B.cap_stream);
+        if (B.dev)
+            cudaFree(B.dev);
+        if (B.host)
+            cudaFreeHost(B.host);
+        const int keep = B.tuned_ns;
+        B = BatchState();
+        B.tuned_ns = keep;
+    }
+    cudaSetDevice(cur);
+    return QBF_OK;
+}
+
+}  // namespace qbf

@@ -66,4 +66,16 @@ struct DevResult {
     unsigned long long n_candidates;
 };
 
+// One instance of a batched solve (written by the host, read by the kernels).
+struct BatchDesc {
+    const void *Q;                 // caller's matrix, n_src x n_src, row-major
+    int n_src;                     // caller's n
+    int n;                         // walk dimension (>= n_src; extra variables are zero)
+    int dtype;
+    int ns;                        // suffix bits walked per lane
+    unsigned long long nprefix;    // 2^(n - ns)
+    unsigned long long item_off;   // first global work item (32 prefixes each)
+    unsigned long long rec_off;    // first walk record
+};
+
 }  // namespace qbf

@@ -12,6 +12,8 @@ constexpr int kModeMin = 0;
 constexpr int kModeEmit = 1;
 constexpr int kModeTrace = 2;
 constexpr unsigned long long kCandCap = 1ull << 22;  // candidate states per solve
+// tables_kernel output: K[2][64] in-block corrections
+constexpr int kKbufInts = 128;
 
 struct WalkArgs {
     int n;                          // variables
@@ -19,7 +21,8 @@ struct WalkArgs {
     unsigned long long p_lo, p_hi;  // MIN/TRACE: prefixes [p_lo, p_hi)
     unsigned long long nitems;      // MIN/TRACE: warp items = ceil((p_hi - p_lo) / 32)
     int q;                          // EMIT: sub-prefix bits per flagged prefix
-    int lowest_mode;                // EMIT: walk only the lowest flagged prefix
+    int top_k;                      // EMIT: with top_k = 1 and an exact plan (W = 0)
+                                    // only the lowest flagged prefix is re-walked
     const unsigned int *flagged;    // EMIT: flagged prefixes (absolute, n - ns - q bits)
     Counters *ctr;
     int *pmin;                      // MIN: per-prefix minimum, index p - p_lo
@@ -31,6 +34,8 @@ struct WalkArgs {
 
 // qbf_prepare.cu
 __global__ void prepare_kernel(const void *Q, int n, int dtype, Plan *plan);
+__global__ void batched_prepare_kernel(const BatchDesc *desc, Plan *plans, int *status);
+__global__ void batched_tables_kernel(const BatchDesc *desc, const Plan *plans, Rec *recs, int *K);
 __global__ void tables_kernel(const Plan *plan, int ns, int R, Rec *recs, unsigned nrec, int *Kbuf);
 
 // qbf_walk.cu
@@ -45,8 +50,7 @@ __global__ void reset_counters_kernel(Counters *c);
 __global__ void threshold_kernel(const Plan *plan, const int *pmin, unsigned long long npref,
                                  int top_k, Counters *c);
 __global__ void flag_kernel(const Plan *plan, const int *pmin, unsigned long long npref,
-                            unsigned long long p_lo, int lowest_mode, unsigned int *flagged,
-                            Counters *c);
+                            unsigned long long p_lo, int top_k, unsigned int *flagged, Counters *c);
 __global__ void rescore_kernel(const Plan *plan, const void *Q, int n, int dtype,
                                const unsigned long long *cand, const Counters *c,
                                unsigned long long cap, long long *vals);
@@ -56,6 +60,13 @@ __global__ void select_kernel(const Plan *plan, const unsigned long long *cand,
 
 // qbf_api.cu: report an error through qbf_last_error_string(); returns code
 int record_error(int code, const char *msg);
+
+// qbf_batched.cu
+int solve_batched(const void *const *Q, const int *n, const int *dtype, int count,
+                  const qbf_options *opt, double *min_value, uint64_t *argmin, cudaStream_t s,
+                  int *kernel_launches);
+int set_tuned_batch_ns(int ns);
+int release_batched();
 
 // qbf_microbench.cu
 cudaError_t run_alu_microbench(int op, double *ops_per_clk_sm, double *sm_mhz, double *seconds,

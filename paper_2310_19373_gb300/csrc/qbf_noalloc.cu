@@ -61,7 +61,7 @@ NaLayout na_layout(int ns, int R, unsigned long long npref)
     L.res = o;
     o = al256(o + sizeof(DevResult));
     L.kbuf = o;
-    o = al256(o + sizeof(int) * 128);
+    o = al256(o + sizeof(int) * kKbufInts);
     L.recs = o;
     o = al256(o + sizeof(Rec) * std::max<size_t>((size_t)1 << (ns - R), 2));
     L.pmin = o;
@@ -207,19 +207,18 @@ int solve_noalloc_locked(const void *Q, int n, int dtype, const qbf_options *opt
     threshold_kernel<<<1, 1024, 0, s>>>(plan, pmin, npref, o.top_k, ctr);
     NA_CUDA(cudaGetLastError(), "threshold_kernel launch failed");
     const bool is_int = (dtype == QBF_I32 || dtype == QBF_I16);
-    const int lowest_mode = (o.top_k == 1 && is_int) ? 1 : 0;
     const int fb = (int)std::min<unsigned long long>((npref + 255) / 256, 4096);
-    flag_kernel<<<fb, 256, 0, s>>>(plan, pmin, npref, p_lo, lowest_mode, flagged, ctr);
+    flag_kernel<<<fb, 256, 0, s>>>(plan, pmin, npref, p_lo, o.top_k, flagged, ctr);
     NA_CUDA(cudaGetLastError(), "flag_kernel launch failed");
     WalkArgs e = a;
     e.ns = ns - q;
     e.q = q;
-    e.lowest_mode = lowest_mode;
+    e.top_k = o.top_k;
     e.flagged = flagged;
     e.cand = cand;
     e.cand_cap = kNaCandCap;
     e.pmin = nullptr;
-    const unsigned long long max_items = ((lowest_mode ? 1ull : npref) << q) / 32 + 1;
+    const unsigned long long max_items = (npref << q) / 32 + 1;
     NA_CUDA(launch_walk(kModeEmit, R, plan, recs, e, na_grid(R, kModeEmit, n, e.ns, max_items), s),
             "walk (emit) launch failed");
     rescore_kernel<<<256, 256, 0, s>>>(plan, Q, n, dtype, cand, ctr, kNaCandCap, vals);

@@ -64,7 +64,10 @@ __device__ long long block_sum_ll(long long x, long long *red)
 
 }  // namespace
 
-__global__ void __launch_bounds__(256) prepare_kernel(const void *Q, int n, int dtype, Plan *plan)
+// One CTA of 256 threads prepares one instance.  The walk dimension n may
+// exceed the caller's n_src: the extra variables get zero rows and columns
+// (used to give tiny instances of a batch the minimum walk width).
+__device__ void prepare_body(const void *Q, int n_src, int n, int dtype, Plan *plan)
 {
     __shared__ double sQ[kMaxN * kMaxN];
     __shared__ double redd[256];
@@ -75,7 +78,8 @@ __global__ void __launch_bounds__(256) prepare_kernel(const void *Q, int n, int 
 
     int bad = 0;
     for (int e = t; e < nn; e += blockDim.x) {
-        double q = load_q(Q, dtype, e);
+        const int qi = e / n, qj = e % n;
+        double q = (qi < n_src && qj < n_src) ? load_q(Q, dtype, qi * n_src + qj) : 0.0;
         if (!isfinite(q))
             bad = 1;
         sQ[e] = q;
@@ -183,18 +187,21 @@ __global__ void __launch_bounds__(256) prepare_kernel(const void *Q, int n, int 
     }
 }
 
+__global__ void __launch_bounds__(256) prepare_kernel(const void *Q, int n, int dtype, Plan *plan)
+{
+    prepare_body(Q, n, n, dtype, plan);
+}
+
 // Records and in-block corrections for a walk over suffix bits 0..ns-1 with
 // R low bits unrolled (M = ns - R mid bits, 2^M blocks).  Record B (1 <= B < 2^M)
-// describes the flip at the start of block B; entry 0 is unused.
-__global__ void tables_kernel(const Plan *__restrict__ plan, int ns, int R, Rec *recs,
-                              unsigned nrec, int *Kbuf)
+// describes the flip at the start of block B; entry 0 is unused.  The thread
+// with B == 0 writes the corrections K.
+__device__ void tables_body(const Plan *__restrict__ plan, int ns, int R, Rec *recs,
+                            unsigned nrec, int *Kbuf, unsigned B)
 {
-    if (plan->status != QBF_OK)
-        return;
     const int n = plan->n;
     const int *S = plan->S;
     const int *lin = plan->lin;
-    const unsigned B = blockIdx.x * blockDim.x + threadIdx.x;
 
     if (B == 0) {
         // K[pi][u]: static part of the delta at in-block step u of a block of parity pi.
@@ -250,6 +257,39 @@ __global__ void tables_kernel(const Plan *__restrict__ plan, int ns, int R, Rec 
         r.W[i] = (int)w;
     }
     recs[B] = r;
+}
+
+__global__ void tables_kernel(const Plan *__restrict__ plan, int ns, int R, Rec *recs,
+                              unsigned nrec, int *Kbuf)
+{
+    if (plan->status != QBF_OK)
+        return;
+    tables_body(plan, ns, R, recs, nrec, Kbuf, blockIdx.x * blockDim.x + threadIdx.x);
+}
+
+// ---- batched: one CTA per instance ---------------------------------------
+
+__global__ void __launch_bounds__(256) batched_prepare_kernel(const BatchDesc *desc, Plan *plans,
+                                                              int *status)
+{
+    const BatchDesc d = desc[blockIdx.x];
+    Plan *plan = plans + blockIdx.x;
+    prepare_body(d.Q, d.n_src, d.n, d.dtype, plan);
+    if (threadIdx.x == 0)
+        status[blockIdx.x] = plan->status;
+}
+
+__global__ void __launch_bounds__(256) batched_tables_kernel(const BatchDesc *desc,
+                                                             const Plan *plans, Rec *recs, int *K)
+{
+    const int i = blockIdx.x;
+    const Plan *plan = plans + i;
+    if (plan->status != QBF_OK)
+        return;
+    const BatchDesc d = desc[i];
+    const unsigned nrec = 1u << (d.ns - kRMax);
+    for (unsigned B = threadIdx.x; B < nrec; B += blockDim.x)
+        tables_body(plan, d.ns, kRMax, recs + d.rec_off, nrec, K + i * 128, B);
 }
 
 }  // namespace qbf

@@ -9,9 +9,9 @@
 //                     top-k then has a fixed-point value <= tau: the k
 //                     smallest prefix minima are k distinct states whose
 //                     fixed-point values are <= tau - W.
-//   flag_kernel       lists the prefixes with pmin <= tau (or, for an exact
-//                     top-1 with W = 0, only the lowest such prefix: its
-//                     lowest tied state has the lowest natural index).
+//   flag_kernel       lists the prefixes with pmin <= tau (or, for a top-1
+//                     solve with exact values, W = 0, only the lowest such
+//                     prefix: its lowest tied state has the lowest index).
 //   rescore_kernel    evaluates every emitted candidate state from the
 //                     caller's Q: the FP64 canonical sum for float Q (the
 //                     order every FP64 value in this project uses), the exact
@@ -99,11 +99,11 @@ __global__ void __launch_bounds__(1024) threshold_kernel(const Plan *plan, const
 }
 
 __global__ void flag_kernel(const Plan *plan, const int *pmin, unsigned long long npref,
-                            unsigned long long p_lo, int lowest_mode, unsigned int *flagged,
-                            Counters *c)
+                            unsigned long long p_lo, int top_k, unsigned int *flagged, Counters *c)
 {
     if (plan->status != QBF_OK)
         return;
+    const int lowest_mode = (top_k == 1 && plan->window == 0);
     const int tau = c->tau;
     for (unsigned long long e = blockIdx.x * (unsigned long long)blockDim.x + threadIdx.x;
          e < npref; e += (unsigned long long)gridDim.x * blockDim.x) {

@@ -38,6 +38,7 @@
 
 #include "qbf_internal.cuh"
 #include "qbf_kernels.cuh"
+#include "qbf_walk_core.cuh"
 
 namespace qbf {
 
@@ -45,76 +46,10 @@ __constant__ int c_K[2][64];
 
 namespace {
 
-__host__ __device__ constexpr int ctz_c(int u)
-{
-    int l = 0;
-    while (!((u >> l) & 1))
-        ++l;
-    return l;
-}
-
-struct Visitor {
-    int mode;
-    int m;
-    int tau;
-    unsigned long long pbase;  // p << ns
-    unsigned long long slot0;  // trace slot of t = 0
-    Counters *ctr;
-    unsigned long long *cand;
-    unsigned long long cap;
-    unsigned long long *tidx;
-    long long *tval;
-    bool active;
+// corrections from the constant bank (one instance per launch)
+struct ConstK {
+    __device__ __forceinline__ int get(int pi, int u) const { return c_K[pi][u]; }
 };
-
-template <int MODE>
-__device__ __forceinline__ void visit(Visitor &vs, unsigned v, unsigned t)
-{
-    if constexpr (MODE == kModeMin) {
-        vs.m = min(vs.m, (int)v);
-    } else if constexpr (MODE == kModeEmit) {
-        if ((int)v <= vs.tau && vs.active) {
-            unsigned long long pos = atomicAdd(&vs.ctr->cand, 1ull);
-            if (pos < vs.cap)
-                vs.cand[pos] = vs.pbase | (unsigned long long)(t ^ (t >> 1));
-        }
-    } else {
-        if (vs.active) {
-            vs.tidx[vs.slot0 + t] = vs.pbase | (unsigned long long)(t ^ (t >> 1));
-            vs.tval[vs.slot0 + t] = (long long)(int)v;
-        }
-    }
-}
-
-template <int R, int PI, int MODE>
-__device__ __forceinline__ void walk_block(unsigned &v, const unsigned (&GL)[R], unsigned B,
-                                           Visitor &vs)
-{
-#pragma unroll
-    for (int u = 1; u < (1 << R); ++u) {
-        const int l = ctz_c(u);
-        const int g = u ^ (u >> 1);
-        const int nb = ((g >> l) & 1) ^ ((l == R - 1) ? PI : 0);
-        const unsigned d = nb ? GL[l] : 0u - GL[l];
-        v = v + d + (unsigned)c_K[PI][u];
-        visit<MODE>(vs, v, (B << R) | (unsigned)u);
-    }
-}
-
-template <int R, int MODE>
-__device__ __forceinline__ void block_transition(unsigned &v, unsigned (&GL)[R], const int4 ra,
-                                                 const int4 rb, const int *sC, unsigned B,
-                                                 Visitor &vs)
-{
-    // ra = (T, code, W0, W1), rb = (W2, W3, W4, W5)
-    const int c = sC[ra.y * blockDim.x + threadIdx.x];
-    v = v + (unsigned)ra.x + (unsigned)c;
-    visit<MODE>(vs, v, B << R);
-    const int W[6] = {ra.z, ra.w, rb.x, rb.y, rb.z, rb.w};
-#pragma unroll
-    for (int i = 0; i < R; ++i)
-        GL[i] += (unsigned)W[i];
-}
 
 }  // namespace
 
@@ -126,7 +61,6 @@ __global__ void __launch_bounds__(kWalkThreads) walk_split_kernel(const Plan *__
     extern __shared__ int smem[];
     const int n = a.n;
     const int ns = a.ns;
-    const int kp = n - ns;
     int *sS = smem;
     int *sLin = sS + n * n;
     int *sC = sLin + n;
@@ -139,16 +73,15 @@ __global__ void __launch_bounds__(kWalkThreads) walk_split_kernel(const Plan *__
         return;
 
     const int lane = threadIdx.x & 31;
-    const int M = ns - R;
-    const unsigned nblocks = 1u << M;
     const int4 *rec4 = reinterpret_cast<const int4 *>(recs);
 
     unsigned long long nitems;
     unsigned long long total = 0;
     unsigned long long nflag = 0;
+    const int lowest_mode = (MODE == kModeEmit) && a.top_k == 1 && plan->window == 0;
     if constexpr (MODE == kModeEmit) {
-        nflag = a.lowest_mode ? 1ull : (unsigned long long)a.ctr->flagged;
-        if (a.lowest_mode && a.ctr->lowest == 0xFFFFFFFFu)
+        nflag = lowest_mode ? 1ull : (unsigned long long)a.ctr->flagged;
+        if (lowest_mode && a.ctr->lowest == 0xFFFFFFFFu)
             nflag = 0;
         total = nflag << a.q;
         nitems = (total + 31) >> 5;
@@ -156,14 +89,7 @@ __global__ void __launch_bounds__(kWalkThreads) walk_split_kernel(const Plan *__
         nitems = a.nitems;
     }
 
-    Visitor vs;
-    vs.mode = MODE;
-    vs.tau = (MODE == kModeEmit) ? a.ctr->tau : 0;
-    vs.ctr = a.ctr;
-    vs.cand = a.cand;
-    vs.cap = a.cand_cap;
-    vs.tidx = a.trace_idx;
-    vs.tval = a.trace_val;
+    const int tau = (MODE == kModeEmit) ? a.ctr->tau : 0;
 
     while (true) {
         unsigned long long item = 0;
@@ -180,73 +106,66 @@ __global__ void __launch_bounds__(kWalkThreads) walk_split_kernel(const Plan *__
             unsigned long long i = item * 32 + lane;
             active = i < total;
             unsigned long long ic = active ? i : total - 1;
-            unsigned long long fp = a.lowest_mode ? (unsigned long long)a.ctr->lowest
-                                                  : (unsigned long long)a.flagged[ic >> a.q];
+            unsigned long long fp = lowest_mode ? (unsigned long long)a.ctr->lowest
+                                                : (unsigned long long)a.flagged[ic >> a.q];
             p = (fp << a.q) | (ic & ((1ull << a.q) - 1));
         } else {
             unsigned long long i = a.p_lo + item * 32 + lane;
             active = i < a.p_hi;
             p = active ? i : a.p_lo;
         }
-        vs.active = active;
-        vs.pbase = p << ns;
-        vs.slot0 = (p - a.p_lo) << ns;
+        const unsigned long long pbase = p << ns;
+        const unsigned long long slot0 = (p - a.p_lo) << ns;
 
         // value of (prefix, suffix = 0) and the lane parts of the suffix fields
-        unsigned v = 0;
-        for (int j = 0; j < kp; ++j) {
-            if (!((p >> j) & 1))
-                continue;
-            const int i = ns + j;
-            unsigned row = (unsigned)sLin[i];
-            for (int jj = j + 1; jj < kp; ++jj)
-                if ((p >> jj) & 1)
-                    row += (unsigned)sS[i * n + ns + jj];
-            v += row;
-        }
         unsigned GL[R];
-#pragma unroll
-        for (int i = 0; i < R; ++i) {
-            unsigned c = (unsigned)sLin[i];
-            for (int j = 0; j < kp; ++j)
-                if ((p >> j) & 1)
-                    c += (unsigned)sS[i * n + ns + j];
-            GL[i] = c;
-        }
-        for (int i = R; i < ns; ++i) {
-            unsigned c = 0;
-            for (int j = 0; j < kp; ++j)
-                if ((p >> j) & 1)
-                    c += (unsigned)sS[i * n + ns + j];
-            sC[(2 * (i - R) + 1) * blockDim.x + threadIdx.x] = (int)c;
-            sC[(2 * (i - R)) * blockDim.x + threadIdx.x] = (int)(0u - c);
-        }
+        unsigned v = lane_setup<R>(p, n, ns, sS, sLin, sC, blockDim.x, threadIdx.x, GL);
 
         // ---- A3/A4: the walk -------------------------------------------
-        vs.m = (int)v;
-        if constexpr (MODE != kModeMin)
-            visit<MODE>(vs, v, 0u);
-        if (M == 0) {
-            walk_block<R, 0, MODE>(v, GL, 0u, vs);
-        } else {
-            for (unsigned B = 0; B < nblocks; B += 2) {
-                const int4 r1a = __ldg(rec4 + 2 * (B + 1));
-                const int4 r1b = __ldg(rec4 + 2 * (B + 1) + 1);
-                const unsigned B2 = (B + 2 < nblocks) ? B + 2 : B + 1;
-                const int4 r2a = __ldg(rec4 + 2 * B2);
-                const int4 r2b = __ldg(rec4 + 2 * B2 + 1);
-                walk_block<R, 0, MODE>(v, GL, B, vs);
-                block_transition<R, MODE>(v, GL, r1a, r1b, sC, B + 1, vs);
-                walk_block<R, 1, MODE>(v, GL, B + 1, vs);
-                if (B + 2 < nblocks)
-                    block_transition<R, MODE>(v, GL, r2a, r2b, sC, B + 2, vs);
+        int m = (int)v;
+        if constexpr (MODE == kModeMin) {
+            m = walk_suffix_min<R>(v, GL, ns, rec4, sC, blockDim.x, threadIdx.x, ConstK());
+        } else if (MODE == kModeEmit && lowest_mode) {
+            // exact values (W = 0), top-1: only the lowest tied index of each
+            // lane can win, so each lane emits that one state
+            unsigned long long best = ~0ull;
+            walk_suffix_visit<R>(v, GL, ns, rec4, sC, blockDim.x, threadIdx.x, ConstK(),
+                                 [&](unsigned val, unsigned t) {
+                                     if ((int)val <= tau) {
+                                         const unsigned long long x =
+                                             pbase | (unsigned long long)(t ^ (t >> 1));
+                                         best = x < best ? x : best;
+                                     }
+                                 });
+            if (active && best != ~0ull) {
+                unsigned long long pos = atomicAdd(&a.ctr->cand, 1ull);
+                if (pos < a.cand_cap)
+                    a.cand[pos] = best;
             }
+        } else if constexpr (MODE == kModeEmit) {
+            walk_suffix_visit<R>(v, GL, ns, rec4, sC, blockDim.x, threadIdx.x, ConstK(),
+                                 [&](unsigned val, unsigned t) {
+                                     if ((int)val <= tau && active) {
+                                         unsigned long long pos = atomicAdd(&a.ctr->cand, 1ull);
+                                         if (pos < a.cand_cap)
+                                             a.cand[pos] = pbase | (unsigned long long)(t ^ (t >> 1));
+                                     }
+                                 });
+        } else {
+            walk_suffix_visit<R>(v, GL, ns, rec4, sC, blockDim.x, threadIdx.x, ConstK(),
+                                 [&](unsigned val, unsigned t) {
+                                     if (active) {
+                                         a.trace_idx[slot0 + t] =
+                                             pbase | (unsigned long long)(t ^ (t >> 1));
+                                         a.trace_val[slot0 + t] = (long long)(int)val;
+                                     }
+                                 });
         }
 
         if constexpr (MODE == kModeMin) {
             if (active)
-                a.pmin[p - a.p_lo] = vs.m;
-            int wm = active ? vs.m : INT_MAX;
+                a.pmin[p - a.p_lo] = m;
+            int wm = active ? m : INT_MAX;
 #pragma unroll
             for (int o = 16; o > 0; o >>= 1)
                 wm = min(wm, __shfl_xor_sync(0xffffffffu, wm, o));

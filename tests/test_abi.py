@@ -50,7 +50,7 @@ def test_struct_sizes_match_header():
     from paper_2310_19373_gb300 import _binding
 
     # qbf_options: 4 ints + uint64 + 8 ints; qbf_result: see include/qbf.h
-    assert ctypes.sizeof(_binding.QbfOptions) == 4 * 4 + 8 + 8 * 4
+    assert ctypes.sizeof(_binding.QbfOptions) == 4 * 4 + 8 + 8 * 4  # 2 named + 6 reserved ints
     exp = 8 + 8 + 4 + 4 + 8 * 64 + 8 * 64 + 4 + 4 + 8 + 8 + 4 + 4 + 4 + 4 + 8 + 4 + 3 * 4
     assert ctypes.sizeof(_binding.QbfResult) == exp
 

@@ -82,6 +82,33 @@ def test_trace_flip_sequence_is_binary_carry():
         assert flips == [((t & -t).bit_length() - 1) for t in range(1, 1 << ns)]
 
 
+def _fixed_point_image(Q, sigma):
+    Qd = np.asarray(Q, dtype=np.float64)
+    n = Qd.shape[0]
+    S = np.rint(np.ldexp(Qd + Qd.T, sigma)).astype(np.int64)
+    Qhat = np.triu(S, 1)
+    Qhat[np.diag_indices(n)] = np.rint(np.ldexp(np.diag(Qd), sigma)).astype(np.int64)
+    return Qhat
+
+
+@pytest.mark.parametrize("n,k", [(1, 0), (3, 2), (6, 0), (7, 1), (9, 3), (12, 4), (13, 2),
+                                 (15, 7), (16, 10), (17, 6), (20, 8)])
+@pytest.mark.parametrize("kind", ["int", "float"])
+def test_min_walk_prefix_minima(n, k, kind):
+    """The production MIN walk's per-prefix minima equal the oracle's, prefix by prefix."""
+    rng = np.random.default_rng(77 * n + k)
+    if kind == "int":
+        Q = rng.integers(-100, 101, size=(n, n)).astype(np.int32)
+    else:
+        Q = rng.normal(size=(n, n)).astype(np.float32)
+    pm, sigma = qb.prefix_minima(dev(Q), k)
+    pm = pm.cpu().numpy()
+    Qhat = Q.astype(np.int64) if kind == "int" else _fixed_point_image(Q, sigma)
+    ns = n - k
+    want = [oracle.brute_min(Qhat, p << ns, (p + 1) << ns)[0] for p in range(1 << k)]
+    assert pm.tolist() == want
+
+
 # ---------------------------------------------------------------- hand-worked
 
 
@@ -187,6 +214,11 @@ def test_edge_cases():
     for dt in (np.int32, np.float32, np.float64):
         s = qb.solve(dev(np.zeros((22, 22), dtype=dt)), top_k=3)
         assert s.min_value == 0 and s.topk_indices == [0, 1, 2]
+    # large all-zero matrices with top-1: exact values, only the lowest tied
+    # state of each lane of the lowest prefix is re-examined
+    for dt, n in ((np.float32, 30), (np.int32, 40), (np.float64, 33)):
+        s = qb.solve(dev(np.zeros((n, n), dtype=dt)))
+        assert (s.min_value, s.argmin) == (0, 0) and s.n_candidates <= 1 << 12
     # a variable with an all-zero row and column ties every state with its twin
     Q = inputs.uniform_int(16, seed=9)
     Q[5, :] = 0
