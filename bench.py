@@ -229,6 +229,20 @@ def run_variants(dev, flush):
                                        "half int16 uniform{-50..50}, seed 0; one persistent walk "
                                        "under a CUDA graph",
                            "states": states, "seconds": t, "states_per_s": states / t}
+    # log Z forward and backward: 64 instances, n = 28, N(0, 1/n), beta in {0.1, 1, 10}
+    QL = torch.from_numpy(inputs.config_logz()).to(dev)
+    betas = list(inputs.LOGZ_BETAS)
+    sp = stream.cuda_stream
+    grad = torch.empty((64, 28, 28), dtype=torch.float64, device=dev)
+    t_f = timed(lambda: qb.qbf_logz(QL.data_ptr(), 28, qb.QBF_F32, 64, betas, sp), reps=2)
+    t_b = timed(lambda: qb.qbf_logz_backward(QL.data_ptr(), 28, qb.QBF_F32, 64, betas, None,
+                                             grad.data_ptr(), None, sp), reps=2)
+    st = 64.0 * 2 ** 28
+    out["logz_64x28"] = {"workload": "64 QUBOs n=28 FP32 N(0,1/n), beta in {0.1,1,10}; forward "
+                                     "= certified min + log Z for 3 betas, backward = -beta "
+                                     "E[xx^T] for 3 betas",
+                         "states": st, "forward_seconds": t_f, "backward_seconds": t_b,
+                         "forward_states_per_s": st / t_f}
     # n = 32 int32 (dense), exact
     Q32 = torch.from_numpy(inputs.config_n32_int(0)).to(dev)
     t = timed(lambda: qb.solve(Q32))

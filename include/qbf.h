@@ -174,6 +174,48 @@ int qbf_tune_batched(const void *const *Q_dev, const int *n, const int *dtype, i
                      void *stream);
 
 /*
+ * qbf_logz -- exact Boltzmann log-partition log Z(Q, beta) = log sum_x
+ * exp(-beta x^T Q x) of `batch` instances, by the same Gray-code walk.
+ *
+ * Q_dev   : device, batch * n * n elements of dtype, instance b at offset b*n*n.
+ * n       : 2 .. QBF_BATCH_MAX_N.  batch: 1 .. 4096.  beta: host, nbeta (1..8)
+ *           values, each finite and > 0.
+ * logz    : host, batch * nbeta (logz[b * nbeta + j]).
+ * min_value, argmin : host, batch entries; the certified minimum and lowest
+ *           argmin (as qbf_solve_batched), which also fix the shift m.
+ * Energies come from an exact two-limb fixed-point image of Q (resolution
+ * 2^-(sigma+16) of f); weights exp(-beta (f - m)) are FP32, summed in FP32 per
+ * block, Kahan-compensated per thread and in FP64 across threads.
+ */
+int qbf_logz(const void *Q_dev, int n, int dtype, int batch, const double *beta, int nbeta,
+             double *logz, double *min_value, uint64_t *argmin, void *stream);
+
+/*
+ * qbf_logz_backward -- gradient of sum_{b,j} upstream[b,j] * log Z(Q_b, beta_j).
+ *
+ * d log Z / d Q_ij = -beta E_beta[x_i x_j] for every entry (f uses every Q_ij).
+ * upstream_dev : device, batch * nbeta doubles, or NULL for all ones.
+ * grad_dev     : device, batch * n * n doubles (overwritten).
+ * moment_dev   : device, batch * nbeta * n * n doubles receiving E_beta[x x^T],
+ *                or NULL.
+ * Re-walks the enumeration: a walk with the top ceil(n/2) variables fixed per
+ * thread gives per-thread sums of w and w * x_j, a second walk on the rotated
+ * variable order gives the remaining block.
+ */
+int qbf_logz_backward(const void *Q_dev, int n, int dtype, int batch, const double *beta,
+                      int nbeta, const double *upstream_dev, double *grad_dev, double *moment_dev,
+                      void *stream);
+
+/*
+ * qbf_danskin -- subgradient of min_x x^T Q x: grad[b] = upstream[b] x* x*^T
+ * with x* the lowest-index argmin (argmin_host from qbf_solve_batched or
+ * qbf_logz).  upstream_dev: device, batch doubles or NULL (ones);
+ * grad_dev: device, batch * n * n doubles.
+ */
+int qbf_danskin(const uint64_t *argmin_host, int n, int batch, const double *upstream_dev,
+                double *grad_dev, void *stream);
+
+/*
  * qbf_solve_noalloc -- qbf_solve without any memory allocation by the call.
  *
  * The paper has no counterpart: this is a deployment variant of qbf_solve for

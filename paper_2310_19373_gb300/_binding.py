@@ -84,6 +84,15 @@ _SIGS = {
                                         ctypes.POINTER(ctypes.c_int), ctypes.c_int, ctypes.c_int,
                                         ctypes.c_int, ctypes.POINTER(ctypes.c_int),
                                         ctypes.POINTER(ctypes.c_double), _VP]),
+    "qbf_logz": (ctypes.c_int, [_VP, ctypes.c_int, ctypes.c_int, ctypes.c_int,
+                                ctypes.POINTER(ctypes.c_double), ctypes.c_int,
+                                ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double),
+                                ctypes.POINTER(ctypes.c_uint64), _VP]),
+    "qbf_logz_backward": (ctypes.c_int, [_VP, ctypes.c_int, ctypes.c_int, ctypes.c_int,
+                                         ctypes.POINTER(ctypes.c_double), ctypes.c_int, _VP, _VP,
+                                         _VP, _VP]),
+    "qbf_danskin": (ctypes.c_int, [ctypes.POINTER(ctypes.c_uint64), ctypes.c_int, ctypes.c_int,
+                                   _VP, _VP, _VP]),
     "qbf_solve_noalloc": (ctypes.c_int, [_VP, ctypes.c_int, ctypes.c_int,
                                          ctypes.POINTER(QbfOptions), ctypes.POINTER(QbfResult),
                                          _VP]),
@@ -189,6 +198,35 @@ def solve_batched(Qs, batch_suffix_bits: int = 0, stream=None):
     s = stream if stream is not None else torch.cuda.current_stream().cuda_stream
     return qbf_solve_batched([q.data_ptr() for q in Qs], [q.shape[0] for q in Qs],
                              [dtype_code(q) for q in Qs], opt, s)
+
+
+def qbf_logz(Q_dev: int, n: int, dtype: int, batch: int, betas, stream: int | None = None):
+    """Returns (logz[batch][nbeta], min_values[batch], argmins[batch])."""
+    nb = len(betas)
+    B = (ctypes.c_double * nb)(*[float(b) for b in betas])
+    lz = (ctypes.c_double * (batch * nb))()
+    vm = (ctypes.c_double * batch)()
+    am = (ctypes.c_uint64 * batch)()
+    rc = lib().qbf_logz(_VP(Q_dev), n, dtype, batch, B, nb, lz, vm, am, _VP(stream or 0))
+    _check(rc)
+    return ([list(lz[b * nb:(b + 1) * nb]) for b in range(batch)], list(vm),
+            [int(v) for v in am])
+
+
+def qbf_logz_backward(Q_dev: int, n: int, dtype: int, batch: int, betas, upstream_dev,
+                      grad_dev: int, moment_dev, stream: int | None = None) -> None:
+    nb = len(betas)
+    B = (ctypes.c_double * nb)(*[float(b) for b in betas])
+    rc = lib().qbf_logz_backward(_VP(Q_dev), n, dtype, batch, B, nb, _VP(upstream_dev or 0),
+                                 _VP(grad_dev), _VP(moment_dev or 0), _VP(stream or 0))
+    _check(rc)
+
+
+def qbf_danskin(argmins, n: int, batch: int, upstream_dev, grad_dev: int,
+                stream: int | None = None) -> None:
+    A = (ctypes.c_uint64 * batch)(*[int(a) for a in argmins])
+    rc = lib().qbf_danskin(A, n, batch, _VP(upstream_dev or 0), _VP(grad_dev), _VP(stream or 0))
+    _check(rc)
 
 
 def qbf_solve_noalloc(Q_dev: int, n: int, dtype: int, opt: QbfOptions | None,
@@ -340,3 +378,70 @@ def walk_trace(Q, prefix_bits: int):
     sigma = qbf_walk_trace(Q.data_ptr(), n, dtype_code(Q), prefix_bits, idx.data_ptr(),
                            val.data_ptr(), s)
     return idx, val, sigma
+
+
+# ---- differentiable wrappers ---------------------------------------------
+
+
+def _autograd():
+    import torch
+
+    class LogZFn(torch.autograd.Function):
+        """log Z(Q_b, beta_j) for a batch Q of shape (batch, n, n); the backward
+        pass re-walks the enumeration on the GPU (qbf_logz_backward)."""
+
+        @staticmethod
+        def forward(ctx, Q, betas):
+            Qc = Q.detach().contiguous()
+            batch, n = Qc.shape[0], Qc.shape[1]
+            s = torch.cuda.current_stream(Qc.device).cuda_stream
+            lz, vmin, am = qbf_logz(Qc.data_ptr(), n, dtype_code(Qc), batch, betas, s)
+            ctx.save_for_backward(Qc)
+            ctx.betas = tuple(float(b) for b in betas)
+            return torch.tensor(lz, dtype=torch.float64, device=Q.device)
+
+        @staticmethod
+        def backward(ctx, g):
+            (Qc,) = ctx.saved_tensors
+            batch, n = Qc.shape[0], Qc.shape[1]
+            up = g.detach().to(torch.float64).contiguous()
+            grad = torch.empty((batch, n, n), dtype=torch.float64, device=Qc.device)
+            s = torch.cuda.current_stream(Qc.device).cuda_stream
+            qbf_logz_backward(Qc.data_ptr(), n, dtype_code(Qc), batch, ctx.betas, up.data_ptr(),
+                              grad.data_ptr(), None, s)
+            return grad.to(Qc.dtype), None
+
+    class MinFn(torch.autograd.Function):
+        """min_x x^T Q_b x for a batch; backward is the Danskin subgradient x* x*^T."""
+
+        @staticmethod
+        def forward(ctx, Q):
+            Qc = Q.detach().contiguous()
+            vmin, am = solve_batched(list(Qc))
+            ctx.argmin = am
+            ctx.n = Qc.shape[1]
+            ctx.dtype = Qc.dtype
+            return torch.tensor(vmin, dtype=torch.float64, device=Q.device)
+
+        @staticmethod
+        def backward(ctx, g):
+            batch = len(ctx.argmin)
+            up = g.detach().to(torch.float64).contiguous()
+            grad = torch.empty((batch, ctx.n, ctx.n), dtype=torch.float64, device=g.device)
+            s = torch.cuda.current_stream(g.device).cuda_stream
+            qbf_danskin(ctx.argmin, ctx.n, batch, up.data_ptr(), grad.data_ptr(), s)
+            return grad.to(ctx.dtype)
+
+    return LogZFn, MinFn
+
+
+def logz(Q, betas):
+    """Differentiable log Z for Q of shape (batch, n, n) on the GPU: (batch, len(betas))."""
+    LogZFn, _ = _autograd()
+    return LogZFn.apply(Q, tuple(betas))
+
+
+def qubo_min(Q):
+    """Differentiable (Danskin) minimum for Q of shape (batch, n, n): (batch,)."""
+    _, MinFn = _autograd()
+    return MinFn.apply(Q)

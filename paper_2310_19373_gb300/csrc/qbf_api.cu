@@ -591,11 +591,33 @@ int qbf_tune_batched(const void *const *Q_dev, const int *n, const int *dtype, i
     return QBF_OK;
 }
 
+int qbf_logz(const void *Q_dev, int n, int dtype, int batch, const double *beta, int nbeta,
+             double *logz, double *min_value, uint64_t *argmin, void *stream)
+{
+    return logz_forward(Q_dev, n, dtype, batch, beta, nbeta, logz, min_value, argmin,
+                        (cudaStream_t)stream);
+}
+
+int qbf_logz_backward(const void *Q_dev, int n, int dtype, int batch, const double *beta,
+                      int nbeta, const double *upstream_dev, double *grad_dev, double *moment_dev,
+                      void *stream)
+{
+    return logz_backward(Q_dev, n, dtype, batch, beta, nbeta, upstream_dev, grad_dev, moment_dev,
+                         (cudaStream_t)stream);
+}
+
+int qbf_danskin(const uint64_t *argmin_host, int n, int batch, const double *upstream_dev,
+                double *grad_dev, void *stream)
+{
+    return danskin(argmin_host, n, batch, upstream_dev, grad_dev, (cudaStream_t)stream);
+}
+
 const char *qbf_last_error_string(void) { return g_err.c_str(); }
 
 int qbf_release(void)
 {
     release_batched();
+    release_logz();
     std::lock_guard<std::mutex> lk(g_mu);
     int cur = 0;
     cudaGetDevice(&cur);

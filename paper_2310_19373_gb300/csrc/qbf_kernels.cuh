@@ -36,6 +36,9 @@ struct WalkArgs {
 __global__ void prepare_kernel(const void *Q, int n, int dtype, Plan *plan);
 __global__ void batched_prepare_kernel(const BatchDesc *desc, Plan *plans, int *status);
 __global__ void batched_tables_kernel(const BatchDesc *desc, const Plan *plans, Rec *recs, int *K);
+__global__ void logz_prepare_kernel(const void *Q, int n, int dtype, int rot, Plan *plans);
+__global__ void logz_tables_kernel(const Plan *plans, int nsA, int nsB, Rec *recs,
+                                   unsigned rec_stride, int *K);
 __global__ void tables_kernel(const Plan *plan, int ns, int R, Rec *recs, unsigned nrec, int *Kbuf);
 
 // qbf_walk.cu
@@ -67,6 +70,15 @@ int solve_batched(const void *const *Q, const int *n, const int *dtype, int coun
                   int *kernel_launches);
 int set_tuned_batch_ns(int ns);
 int release_batched();
+
+// qbf_logz.cu
+int logz_forward(const void *Q, int n, int dtype, int batch, const double *beta, int nbeta,
+                 double *logz, double *min_value, uint64_t *argmin, cudaStream_t s);
+int logz_backward(const void *Q, int n, int dtype, int batch, const double *beta, int nbeta,
+                  const double *upstream, double *grad, double *moment, cudaStream_t s);
+int danskin(const uint64_t *argmin_host, int n, int batch, const double *upstream, double *grad,
+            cudaStream_t s);
+int release_logz();
 
 // qbf_microbench.cu
 cudaError_t run_alu_microbench(int op, double *ops_per_clk_sm, double *sm_mhz, double *seconds,

@@ -1,0 +1,725 @@
+// qbf_logz.cu -- exact Boltzmann log-partition and its gradient by the same
+// Gray-code walk (rows A10, A11).
+//
+//   log Z(Q, beta) = log sum_x exp(-beta f(x)),      f(x) = x^T Q x (Eq. 1)
+//   d log Z / d Q_ij = -beta E_beta[x_i x_j]         (f is linear in every Q_ij)
+//   d min f / d Q_ij = x*_i x*_j                     (Danskin, x* = lowest argmin)
+//
+// Energies.  Each instance is walked on a two-limb fixed-point image
+// (qbf_prepare.cu: hi = round(y 2^s), lo = 16 more bits of the residual), i.e.
+// f at scale 2^(s+16) = hi_value * 2^16 + lo_value, both limbs walked exactly in
+// int32 in lockstep.  The shift m is the image value of the certified argmin
+// (from the batched minimiser), so every weight w = exp(-beta (f - m)) is <= ~1.
+// w = ex2(d_hi * c_hi + d_lo * c_lo) with d the limb differences to m and
+// c = -beta log2(e) 2^-(s or s+16).  Weights are summed in FP32 per block of
+// 2^R states, blocks are added with Kahan compensation per lane, lanes in FP64
+// in a fixed order.
+//
+// Second moment without O(n^2) work per state.  Walk A fixes the top kA
+// variables per lane (prefix p) and walks the bottom nsA: per lane it keeps
+// Z_p = sum_s w and M1_p[j] = sum_s w s_j.  Then
+//   top x top:     sum_p Z_p p_i p_j
+//   top x bottom:  sum_p p_i M1_p[j]
+// Walk B runs on the variables rotated by nsA, so the bottom nsA variables
+// become its prefix, and gives bottom x bottom = sum_p' Z_p' p'_i p'_j from its
+// per-lane Z alone.  Dividing by Z gives E[x_i x_j] for every pair.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <climits>
+#include <cmath>
+#include <cstring>
+#include <mutex>
+#include <string>
+#include <vector>
+
+#include "qbf.h"
+#include "qbf_internal.cuh"
+#include "qbf_kernels.cuh"
+#include "qbf_walk_core.cuh"
+
+namespace qbf {
+
+namespace {
+
+constexpr int kLzThreads = 128;
+constexpr int kLzMaxBeta = 8;
+constexpr int kLzMaxNs = 17;
+
+struct LzArgs {
+    int n, ns, kp, nbeta, R;
+    unsigned long long lanes;   // 2^kp prefixes per instance
+    const Plan *plans;          // (b * 2 + w) * 2 + limb
+    int walk;                   // 0: A, 1: B
+    const Rec *recs;
+    unsigned rec_stride;
+    const int *K;
+    const int *shift;           // per instance and walk: (hi, lo) value of the argmin
+    float ch[kLzMaxBeta], cl[kLzMaxBeta];
+    double *laneZ;              // MODE Z:  [b][lane][beta]
+    double *laneM1;             // MODE M1: [b][lane][ns]
+};
+
+constexpr int kModeZ = 0;   // Z for every beta
+constexpr int kModeM1 = 1;  // Z and M1 for one beta
+
+__device__ __forceinline__ float ex2_approx(float x)
+{
+    float y;
+    asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+
+__device__ __forceinline__ void kahan_add(float &s, float &c, float x)
+{
+    const float y = x - c;
+    const float t = s + y;
+    c = (t - s) - y;
+    s = t;
+}
+
+// Two int32 walks (hi and lo limb) over the same suffix in lockstep; visit is
+// called at every state, flush after every block of 2^R states.
+template <int R, class F, class G>
+__device__ __forceinline__ void walk2(unsigned vh, unsigned (&GLh)[R], unsigned vl,
+                                      unsigned (&GLl)[R], int ns, const int4 *rh, const int4 *rl,
+                                      const int *sCh, const int *sCl, int stride, int slot,
+                                      const int *Kh, const int *Kl, F &&visit, G &&flush)
+{
+    const int M = ns - R;
+    const unsigned nblocks = 1u << M;
+    visit(vh, vl, 0u);
+    for (unsigned B = 0; B < nblocks; ++B) {
+        const int pi = B & 1;
+        if (B > 0) {
+            const int4 ah = __ldg(rh + 2 * B), bh = __ldg(rh + 2 * B + 1);
+            const int4 al = __ldg(rl + 2 * B), bl = __ldg(rl + 2 * B + 1);
+            vh = vh + (unsigned)ah.x + (unsigned)sCh[ah.y * stride + slot];
+            vl = vl + (unsigned)al.x + (unsigned)sCl[al.y * stride + slot];
+            visit(vh, vl, B << R);
+            const int Wh[6] = {ah.z, ah.w, bh.x, bh.y, bh.z, bh.w};
+            const int Wl[6] = {al.z, al.w, bl.x, bl.y, bl.z, bl.w};
+#pragma unroll
+            for (int i = 0; i < R; ++i) {
+                GLh[i] += (unsigned)Wh[i];
+                GLl[i] += (unsigned)Wl[i];
+            }
+        }
+#pragma unroll
+        for (int u = 1; u < (1 << R); ++u) {
+            const int l = ctz_c(u);
+            const int g = u ^ (u >> 1);
+            const int nb = ((g >> l) & 1) ^ ((l == R - 1) ? pi : 0);
+            vh = vh + (nb ? GLh[l] : 0u - GLh[l]) + (unsigned)Kh[pi * 64 + u];
+            vl = vl + (nb ? GLl[l] : 0u - GLl[l]) + (unsigned)Kl[pi * 64 + u];
+            visit(vh, vl, (B << R) | (unsigned)u);
+        }
+        flush();
+    }
+}
+
+template <int R, int MODE>
+__global__ void __launch_bounds__(kLzThreads) logz_walk_kernel(LzArgs a)
+{
+    extern __shared__ int sm[];
+    const int n = a.n, ns = a.ns;
+    const unsigned long long blocks_per_inst = (a.lanes + kLzThreads - 1) / kLzThreads;
+    const int b = (int)(blockIdx.x / blocks_per_inst);
+    const unsigned long long p0 = (blockIdx.x % blocks_per_inst) * kLzThreads;
+    const Plan *ph = a.plans + (size_t)(b * 2 + a.walk) * 2;
+    const Plan *pl = ph + 1;
+    int *sSh = sm, *sSl = sSh + n * n, *sLh = sSl + n * n, *sLl = sLh + n;
+    int *sKh = sLl + n, *sKl = sKh + 128;
+    int *sCh = sKl + 128, *sCl = sCh + 2 * (ns - R) * kLzThreads;
+    for (int e = threadIdx.x; e < n * n; e += blockDim.x) {
+        sSh[e] = ph->S[e];
+        sSl[e] = pl->S[e];
+    }
+    for (int e = threadIdx.x; e < n; e += blockDim.x) {
+        sLh[e] = ph->lin[e];
+        sLl[e] = pl->lin[e];
+    }
+    const int pidx = (b * 2 + a.walk) * 2;
+    for (int e = threadIdx.x; e < 128; e += blockDim.x) {
+        sKh[e] = a.K[pidx * 128 + e];
+        sKl[e] = a.K[(pidx + 1) * 128 + e];
+    }
+    __syncthreads();
+    if (ph->status != QBF_OK)
+        return;
+    const unsigned long long p = p0 + threadIdx.x;
+    const bool active = p < a.lanes;
+    const unsigned long long pp = active ? p : 0;
+    unsigned GLh[R], GLl[R];
+    const unsigned vh = lane_setup<R>(pp, n, ns, sSh, sLh, sCh, kLzThreads, threadIdx.x, GLh);
+    const unsigned vl = lane_setup<R>(pp, n, ns, sSl, sLl, sCl, kLzThreads, threadIdx.x, GLl);
+    const unsigned mh = (unsigned)a.shift[(b * 2 + a.walk) * 2];
+    const unsigned ml = (unsigned)a.shift[(b * 2 + a.walk) * 2 + 1];
+    const int4 *rh = reinterpret_cast<const int4 *>(a.recs + (size_t)pidx * a.rec_stride);
+    const int4 *rl = reinterpret_cast<const int4 *>(a.recs + (size_t)(pidx + 1) * a.rec_stride);
+
+    if constexpr (MODE == kModeZ) {
+        float acc[kLzMaxBeta], sum[kLzMaxBeta], comp[kLzMaxBeta];
+#pragma unroll
+        for (int j = 0; j < kLzMaxBeta; ++j)
+            acc[j] = sum[j] = comp[j] = 0.f;
+        walk2<R>(vh, GLh, vl, GLl, ns, rh, rl, sCh, sCl, kLzThreads, threadIdx.x, sKh, sKl,
+                 [&](unsigned xh, unsigned xl, unsigned) {
+                     const float dh = (float)(int)(xh - mh), dl = (float)(int)(xl - ml);
+#pragma unroll
+                     for (int j = 0; j < kLzMaxBeta; ++j)
+                         if (j < a.nbeta)
+                             acc[j] += ex2_approx(fmaf(dh, a.ch[j], dl * a.cl[j]));
+                 },
+                 [&]() {
+#pragma unroll
+                     for (int j = 0; j < kLzMaxBeta; ++j) {
+                         kahan_add(sum[j], comp[j], acc[j]);
+                         acc[j] = 0.f;
+                     }
+                 });
+        if (active) {
+#pragma unroll
+            for (int j = 0; j < kLzMaxBeta; ++j)
+                if (j < a.nbeta)
+                    a.laneZ[((size_t)b * a.lanes + p) * a.nbeta + j] =
+                        (double)sum[j] - (double)comp[j];
+        }
+    } else {
+        float acc0 = 0.f, sum0 = 0.f, comp0 = 0.f;
+        float acc[kLzMaxNs], sum[kLzMaxNs], comp[kLzMaxNs];
+#pragma unroll
+        for (int j = 0; j < kLzMaxNs; ++j)
+            acc[j] = sum[j] = comp[j] = 0.f;
+        const float ch = a.ch[0], cl = a.cl[0];
+        walk2<R>(vh, GLh, vl, GLl, ns, rh, rl, sCh, sCl, kLzThreads, threadIdx.x, sKh, sKl,
+                 [&](unsigned xh, unsigned xl, unsigned t) {
+                     const float dh = (float)(int)(xh - mh), dl = (float)(int)(xl - ml);
+                     const float w = ex2_approx(fmaf(dh, ch, dl * cl));
+                     const unsigned g = t ^ (t >> 1);
+                     acc0 += w;
+#pragma unroll
+                     for (int j = 0; j < kLzMaxNs; ++j)
+                         if (j < ns && ((g >> j) & 1u))
+                             acc[j] += w;
+                 },
+                 [&]() {
+                     kahan_add(sum0, comp0, acc0);
+                     acc0 = 0.f;
+#pragma unroll
+                     for (int j = 0; j < kLzMaxNs; ++j) {
+                         kahan_add(sum[j], comp[j], acc[j]);
+                         acc[j] = 0.f;
+                     }
+                 });
+        if (active) {
+            a.laneZ[(size_t)b * a.lanes + p] = (double)sum0 - (double)comp0;
+#pragma unroll
+            for (int j = 0; j < kLzMaxNs; ++j)
+                if (j < ns)
+                    a.laneM1[((size_t)b * a.lanes + p) * ns + j] = (double)sum[j] - (double)comp[j];
+        }
+    }
+}
+
+// Image value (hi, lo limbs) of each instance's argmin under both walks' plans.
+__global__ void logz_shift_kernel(const Plan *plans, const unsigned long long *argmin, int n,
+                                  int rot, int *shift)
+{
+    const int b = blockIdx.x;
+    const int w = threadIdx.x >> 1, limb = threadIdx.x & 1;
+    if (threadIdx.x >= 4)
+        return;
+    const Plan *P = plans + (size_t)(b * 2 + w) * 2 + limb;
+    const unsigned long long x = argmin[b];
+    // walk variable v holds the caller's variable (v + rot) mod n in walk B
+    unsigned long long xw = 0;
+    for (int v = 0; v < n; ++v) {
+        const int src = w ? (v + rot) % n : v;
+        xw |= ((x >> src) & 1ull) << v;
+    }
+    unsigned acc = 0;
+    for (int i = 0; i < n; ++i) {
+        if (!((xw >> i) & 1ull))
+            continue;
+        acc += (unsigned)P->lin[i];
+        for (int j = i + 1; j < n; ++j)
+            if ((xw >> j) & 1ull)
+                acc += (unsigned)P->S[i * n + j];
+    }
+    shift[(b * 2 + w) * 2 + limb] = (int)acc;
+}
+
+// deterministic FP64 sum over [0, count) with stride
+__device__ double block_sum_fixed(const double *v, unsigned long long count, size_t stride,
+                                  double *red)
+{
+    double s = 0.0;
+    for (unsigned long long e = threadIdx.x; e < count; e += blockDim.x)
+        s += v[e * stride];
+    red[threadIdx.x] = s;
+    __syncthreads();
+    for (int o = blockDim.x / 2; o > 0; o >>= 1) {
+        if (threadIdx.x < o)
+            red[threadIdx.x] += red[threadIdx.x + o];
+        __syncthreads();
+    }
+    const double r = red[0];
+    __syncthreads();
+    return r;
+}
+
+// log Z per (instance, beta) from walk A's per-lane Z.
+__global__ void __launch_bounds__(256) logz_reduce_kernel(const Plan *plans, const double *laneZ,
+                                                          unsigned long long lanes, int nbeta,
+                                                          const double *beta, const int *shift,
+                                                          double *logz)
+{
+    __shared__ double red[256];
+    const int b = blockIdx.x;
+    const Plan *ph = plans + (size_t)(b * 2) * 2;
+    for (int j = 0; j < nbeta; ++j) {
+        const double Z = block_sum_fixed(laneZ + (size_t)b * lanes * nbeta + j, lanes, nbeta, red);
+        if (threadIdx.x == 0) {
+            if (ph->status != QBF_OK) {
+                logz[b * nbeta + j] = NAN;
+                continue;
+            }
+            const long long m = ((long long)shift[b * 4] << 16) + (long long)shift[b * 4 + 1];
+            const double mreal = ldexp((double)m, -(ph->sigma + 16));
+            logz[b * nbeta + j] = -beta[j] * mreal + log(Z);
+        }
+    }
+}
+
+// E[x_i x_j] for one beta from walk A (Z, M1) and walk B (Z); adds
+// up[b] * (-beta) * E into grad and optionally stores E.
+__global__ void __launch_bounds__(256) logz_moments_kernel(
+    int n, int nsA, unsigned long long lanesA, unsigned long long lanesB, const double *ZA,
+    const double *M1A, const double *ZB, double beta, const double *up, int up_stride,
+    int up_off, double *grad, double *moment, int moment_stride, int moment_off)
+{
+    __shared__ double red[256];
+    const int b = blockIdx.x;
+    const double *za = ZA + (size_t)b * lanesA;
+    const double *m1 = M1A + (size_t)b * lanesA * nsA;
+    const double *zb = ZB + (size_t)b * lanesB;
+    const double ZAt = block_sum_fixed(za, lanesA, 1, red);
+    const double ZBt = block_sum_fixed(zb, lanesB, 1, red);
+    const double u = up ? up[b * up_stride + up_off] : 1.0;
+    const int npair = n * (n + 1) / 2;
+    for (int e = threadIdx.x; e < npair; e += blockDim.x) {
+        // e -> (i, j), i <= j
+        int i = 0, rem = e;
+        while (rem >= n - i) {
+            rem -= n - i;
+            ++i;
+        }
+        const int j = i + rem;
+        double s = 0.0, E;
+        if (i >= nsA) {  // both top: prefix bits of walk A
+            const int bi = i - nsA, bj = j - nsA;
+            for (unsigned long long p = 0; p < lanesA; ++p)
+                if (((p >> bi) & 1ull) && ((p >> bj) & 1ull))
+                    s += za[p];
+            E = s / ZAt;
+        } else if (j >= nsA) {  // i bottom, j top
+            const int bj = j - nsA;
+            for (unsigned long long p = 0; p < lanesA; ++p)
+                if ((p >> bj) & 1ull)
+                    s += m1[p * nsA + i];
+            E = s / ZAt;
+        } else {  // both bottom: prefix bits i, j of walk B
+            for (unsigned long long p = 0; p < lanesB; ++p)
+                if (((p >> i) & 1ull) && ((p >> j) & 1ull))
+                    s += zb[p];
+            E = s / ZBt;
+        }
+        const double gval = u * (-beta) * E;
+        grad[(size_t)b * n * n + i * n + j] += gval;
+        if (i != j)
+            grad[(size_t)b * n * n + j * n + i] += gval;
+        if (moment) {
+            double *mm = moment + (size_t)b * moment_stride + moment_off;
+            mm[i * n + j] = E;
+            mm[j * n + i] = E;
+        }
+    }
+}
+
+__global__ void danskin_kernel(const unsigned long long *argmin, int n, int batch,
+                               const double *up, double *grad)
+{
+    const int b = blockIdx.x;
+    if (b >= batch)
+        return;
+    const unsigned long long x = argmin[b];
+    const double u = up ? up[b] : 1.0;
+    for (int e = threadIdx.x; e < n * n; e += blockDim.x) {
+        const int i = e / n, j = e % n;
+        grad[(size_t)b * n * n + e] = (((x >> i) & 1ull) && ((x >> j) & 1ull)) ? u : 0.0;
+    }
+}
+
+// ------------------------------------------------------------------------
+// host side
+
+std::mutex g_lmu;
+
+struct LzPool {
+    void *dev = nullptr;
+    size_t bytes = 0;
+};
+std::vector<LzPool> g_lpool;
+
+#define L_CUDA(call, where)                                                                      \
+    do {                                                                                         \
+        cudaError_t l_e_ = (call);                                                               \
+        if (l_e_ != cudaSuccess)                                                                 \
+            return record_error(QBF_ECUDA,                                                       \
+                                (std::string(where) + ": " + cudaGetErrorString(l_e_)).c_str()); \
+    } while (0)
+
+size_t al(size_t x) { return (x + 255) & ~(size_t)255; }
+
+struct LzGeo {
+    int n, nsA, kA, nsB, kB, RA, RB;
+    unsigned long long lanesA, lanesB;
+    unsigned rec_stride;
+};
+
+LzGeo lz_geo(int n)
+{
+    LzGeo g;
+    g.n = n;
+    g.nsA = n / 2;
+    g.kA = n - g.nsA;
+    g.nsB = g.kA;
+    g.kB = g.nsA;
+    g.RA = std::min(kRMax, g.nsA);
+    g.RB = std::min(kRMax, g.nsB);
+    g.lanesA = 1ull << g.kA;
+    g.lanesB = 1ull << g.kB;
+    g.rec_stride = 1u << std::max(g.nsA - g.RA, g.nsB - g.RB);
+    return g;
+}
+
+struct LzLayout {
+    size_t plans, recs, K, shift, argmin, laneZA, laneM1, laneZB, beta, total;
+};
+
+LzLayout lz_layout(const LzGeo &g, int batch, int nbeta)
+{
+    LzLayout L;
+    size_t o = 0;
+    auto take = [&](size_t bytes) {
+        size_t at = o;
+        o = al(o + bytes);
+        return at;
+    };
+    L.plans = take(sizeof(Plan) * batch * 4);
+    L.recs = take(sizeof(Rec) * (size_t)g.rec_stride * batch * 4);
+    L.K = take(sizeof(int) * 128 * batch * 4);
+    L.shift = take(sizeof(int) * 4 * batch);
+    L.argmin = take(sizeof(unsigned long long) * batch);
+    L.laneZA = take(sizeof(double) * g.lanesA * batch * std::max(nbeta, 1));
+    L.laneM1 = take(sizeof(double) * g.lanesA * batch * g.nsA);
+    L.laneZB = take(sizeof(double) * g.lanesB * batch);
+    L.beta = take(sizeof(double) * kLzMaxBeta);
+    L.total = o;
+    return L;
+}
+
+int lz_pool(size_t bytes, char **base)
+{
+    int dev = 0;
+    L_CUDA(cudaGetDevice(&dev), "cudaGetDevice");
+    if ((int)g_lpool.size() <= dev)
+        g_lpool.resize(dev + 1);
+    LzPool &P = g_lpool[dev];
+    if (P.bytes < bytes) {
+        L_CUDA(cudaDeviceSynchronize(), "cudaDeviceSynchronize");
+        if (P.dev)
+            cudaFree(P.dev);
+        P.dev = nullptr;
+        P.bytes = 0;
+        L_CUDA(cudaMalloc(&P.dev, bytes), "cudaMalloc(logz scratch)");
+        P.bytes = bytes;
+    }
+    *base = (char *)P.dev;
+    return QBF_OK;
+}
+
+template <int MODE>
+cudaError_t launch_lz(int R, const LzArgs &a, int batch, cudaStream_t s)
+{
+    const size_t smem =
+        sizeof(int) * (2 * a.n * a.n + 2 * a.n + 256 + 2 * 2 * (a.ns - R) * kLzThreads);
+    const unsigned long long bpi = (a.lanes + kLzThreads - 1) / kLzThreads;
+    const unsigned grid = (unsigned)(bpi * batch);
+    auto go = [&](auto kern) {
+        cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             (int)smem);
+        if (e != cudaSuccess)
+            return e;
+        kern<<<grid, kLzThreads, smem, s>>>(a);
+        return cudaGetLastError();
+    };
+    switch (R) {
+    case 1: return go(logz_walk_kernel<1, MODE>);
+    case 2: return go(logz_walk_kernel<2, MODE>);
+    case 3: return go(logz_walk_kernel<3, MODE>);
+    case 4: return go(logz_walk_kernel<4, MODE>);
+    case 5: return go(logz_walk_kernel<5, MODE>);
+    default: return go(logz_walk_kernel<6, MODE>);
+    }
+}
+
+size_t dts(int dt) { return dt == QBF_F64 ? 8 : dt == QBF_I16 ? 2 : (dt == QBF_F32 || dt == QBF_I32) ? 4 : 0; }
+
+int lz_check(const void *Q, int n, int dtype, int batch, const double *beta, int nbeta)
+{
+    if (!Q || !beta)
+        return record_error(QBF_EINVAL, "null pointer argument");
+    if (n < 2 || n > QBF_BATCH_MAX_N)
+        return record_error(QBF_EINVAL, "log Z needs 2 <= n <= 34");
+    if (batch < 1 || batch > 4096)
+        return record_error(QBF_EINVAL, "batch must be in [1, 4096]");
+    if (nbeta < 1 || nbeta > kLzMaxBeta)
+        return record_error(QBF_EINVAL, "nbeta must be in [1, 8]");
+    for (int j = 0; j < nbeta; ++j)
+        if (!(beta[j] > 0.0) || !std::isfinite(beta[j]))
+            return record_error(QBF_EINVAL, "every beta must be finite and > 0");
+    if (dts(dtype) == 0)
+        return record_error(QBF_EDTYPE, "unknown dtype");
+    return QBF_OK;
+}
+
+// certified argmin of every instance (batched minimiser), then the images,
+// tables and shifts shared by the forward and backward walks
+int lz_setup(const void *Q, int n, int dtype, int batch, const LzGeo &g, char *base,
+             const LzLayout &L, double *min_value, uint64_t *argmin, cudaStream_t s)
+{
+    std::vector<const void *> ptrs(batch);
+    std::vector<int> ns(batch, n), dt(batch, dtype);
+    for (int b = 0; b < batch; ++b)
+        ptrs[b] = (const char *)Q + (size_t)b * n * n * dts(dtype);
+    int rc = solve_batched(ptrs.data(), ns.data(), dt.data(), batch, nullptr, min_value, argmin, s,
+                           nullptr);
+    if (rc)
+        return rc;
+    Plan *plans = (Plan *)(base + L.plans);
+    L_CUDA(cudaMemcpyAsync(base + L.argmin, argmin, sizeof(unsigned long long) * batch,
+                           cudaMemcpyHostToDevice, s),
+           "argmin upload");
+    logz_prepare_kernel<<<batch * 2, 256, 0, s>>>(Q, n, dtype, g.nsA, plans);
+    logz_tables_kernel<<<batch * 4, 256, 0, s>>>(plans, g.nsA, g.nsB, (Rec *)(base + L.recs),
+                                                 g.rec_stride, (int *)(base + L.K));
+    logz_shift_kernel<<<batch, 32, 0, s>>>(plans, (const unsigned long long *)(base + L.argmin), n,
+                                           g.nsA, (int *)(base + L.shift));
+    L_CUDA(cudaGetLastError(), "log Z set-up kernels");
+    return QBF_OK;
+}
+
+LzArgs lz_args(const LzGeo &g, char *base, const LzLayout &L, int walk, int nbeta,
+               const double *beta, int sigma_hint)
+{
+    (void)sigma_hint;
+    LzArgs a;
+    memset(&a, 0, sizeof(a));
+    a.n = g.n;
+    a.ns = walk ? g.nsB : g.nsA;
+    a.kp = walk ? g.kB : g.kA;
+    a.R = walk ? g.RB : g.RA;
+    a.lanes = walk ? g.lanesB : g.lanesA;
+    a.nbeta = nbeta;
+    a.plans = (const Plan *)(base + L.plans);
+    a.walk = walk;
+    a.recs = (const Rec *)(base + L.recs);
+    a.rec_stride = g.rec_stride;
+    a.K = (const int *)(base + L.K);
+    a.shift = (const int *)(base + L.shift);
+    a.laneZ = (double *)(base + (walk ? L.laneZB : L.laneZA));
+    a.laneM1 = (double *)(base + L.laneM1);
+    (void)beta;
+    return a;
+}
+
+// c = -beta log2(e) 2^-sigma (hi limb) and 2^-(sigma+16) (lo limb); sigma is
+// per instance but the same for every instance of a batch only by chance, so
+// the kernels get sigma through the plans: the host reads it back first.
+int lz_sigmas(const Plan *plans_dev, int batch, std::vector<int> &sig, cudaStream_t s)
+{
+    sig.assign(batch, 0);
+    for (int b = 0; b < batch; ++b) {
+        L_CUDA(cudaMemcpyAsync(&sig[b], &plans_dev[(size_t)b * 4].sigma, sizeof(int),
+                               cudaMemcpyDeviceToHost, s),
+               "sigma");
+    }
+    L_CUDA(cudaStreamSynchronize(s), "log Z set-up");
+    for (int b = 0; b < batch; ++b) {
+        int st = 0;
+        L_CUDA(cudaMemcpy(&st, &plans_dev[(size_t)b * 4].status, sizeof(int), cudaMemcpyDeviceToHost),
+               "status");
+        if (st != QBF_OK)
+            return record_error(st, ("instance " + std::to_string(b) + ": prepare failed").c_str());
+    }
+    return QBF_OK;
+}
+
+}  // namespace
+
+int logz_forward(const void *Q, int n, int dtype, int batch, const double *beta, int nbeta,
+                 double *logz, double *min_value, uint64_t *argmin, cudaStream_t s)
+{
+    int rc = lz_check(Q, n, dtype, batch, beta, nbeta);
+    if (rc)
+        return rc;
+    if (!logz || !min_value || !argmin)
+        return record_error(QBF_EINVAL, "null pointer argument");
+    std::lock_guard<std::mutex> lk(g_lmu);
+    const LzGeo g = lz_geo(n);
+    const LzLayout L = lz_layout(g, batch, nbeta);
+    char *base = nullptr;
+    if ((rc = lz_pool(L.total, &base)))
+        return rc;
+    if ((rc = lz_setup(Q, n, dtype, batch, g, base, L, min_value, argmin, s)))
+        return rc;
+    std::vector<int> sig;
+    if ((rc = lz_sigmas((const Plan *)(base + L.plans), batch, sig, s)))
+        return rc;
+    // one walk-A launch per distinct sigma (normally one for the whole batch)
+    std::vector<double> Zl;
+    L_CUDA(cudaMemcpyAsync(base + L.beta, beta, sizeof(double) * nbeta, cudaMemcpyHostToDevice, s),
+           "beta upload");
+    std::vector<int> done(batch, 0);
+    for (int b0 = 0; b0 < batch; ++b0) {
+        if (done[b0])
+            continue;
+        // instances sharing sigma b0's value are walked together only if they
+        // form a contiguous run; otherwise walk instance by instance
+        int b1 = b0;
+        while (b1 + 1 < batch && sig[b1 + 1] == sig[b0])
+            ++b1;
+        LzArgs a = lz_args(g, base, L, 0, nbeta, beta, 0);
+        for (int j = 0; j < nbeta; ++j) {
+            const double c = -beta[j] * 1.4426950408889634 * ldexp(1.0, -sig[b0]);
+            a.ch[j] = (float)c;
+            a.cl[j] = (float)(c * ldexp(1.0, -16));
+        }
+        // offset the instance range by adjusting the base pointers
+        a.plans += (size_t)b0 * 4;
+        a.K += (size_t)b0 * 4 * 128;
+        a.recs += (size_t)b0 * 4 * g.rec_stride;
+        a.shift += (size_t)b0 * 4;
+        a.laneZ += (size_t)b0 * g.lanesA * nbeta;
+        L_CUDA(launch_lz<kModeZ>(a.R, a, b1 - b0 + 1, s), "log Z walk");
+        for (int b = b0; b <= b1; ++b)
+            done[b] = 1;
+    }
+    double *dlogz = (double *)(base + L.laneM1);  // reuse: batch * nbeta doubles
+    logz_reduce_kernel<<<batch, 256, 0, s>>>((const Plan *)(base + L.plans),
+                                             (const double *)(base + L.laneZA), g.lanesA, nbeta,
+                                             (const double *)(base + L.beta),
+                                             (const int *)(base + L.shift), dlogz);
+    L_CUDA(cudaGetLastError(), "log Z reduce");
+    L_CUDA(cudaMemcpyAsync(logz, dlogz, sizeof(double) * batch * nbeta, cudaMemcpyDeviceToHost, s),
+           "log Z download");
+    L_CUDA(cudaStreamSynchronize(s), "log Z");
+    return QBF_OK;
+}
+
+int logz_backward(const void *Q, int n, int dtype, int batch, const double *beta, int nbeta,
+                  const double *upstream, double *grad, double *moment, cudaStream_t s)
+{
+    int rc = lz_check(Q, n, dtype, batch, beta, nbeta);
+    if (rc)
+        return rc;
+    if (!grad)
+        return record_error(QBF_EINVAL, "null pointer argument");
+    std::lock_guard<std::mutex> lk(g_lmu);
+    const LzGeo g = lz_geo(n);
+    const LzLayout L = lz_layout(g, batch, 1);
+    char *base = nullptr;
+    if ((rc = lz_pool(L.total, &base)))
+        return rc;
+    std::vector<double> vmin(batch);
+    std::vector<uint64_t> am(batch);
+    if ((rc = lz_setup(Q, n, dtype, batch, g, base, L, vmin.data(), am.data(), s)))
+        return rc;
+    std::vector<int> sig;
+    if ((rc = lz_sigmas((const Plan *)(base + L.plans), batch, sig, s)))
+        return rc;
+    L_CUDA(cudaMemsetAsync(grad, 0, sizeof(double) * batch * n * n, s), "grad clear");
+    for (int j = 0; j < nbeta; ++j) {
+        for (int b = 0; b < batch;) {
+            int b1 = b;
+            while (b1 + 1 < batch && sig[b1 + 1] == sig[b])
+                ++b1;
+            const double c = -beta[j] * 1.4426950408889634 * ldexp(1.0, -sig[b]);
+            for (int walk = 0; walk < 2; ++walk) {
+                LzArgs a = lz_args(g, base, L, walk, 1, beta, 0);
+                a.ch[0] = (float)c;
+                a.cl[0] = (float)(c * ldexp(1.0, -16));
+                a.plans += (size_t)b * 4;
+                a.K += (size_t)b * 4 * 128;
+                a.recs += (size_t)b * 4 * g.rec_stride;
+                a.shift += (size_t)b * 4;
+                a.laneZ += (size_t)b * a.lanes;
+                a.laneM1 += (size_t)b * a.lanes * g.nsA;
+                if (walk == 0)
+                    L_CUDA(launch_lz<kModeM1>(a.R, a, b1 - b + 1, s), "log Z moment walk");
+                else
+                    L_CUDA(launch_lz<kModeZ>(a.R, a, b1 - b + 1, s), "log Z walk (rotated)");
+            }
+            b = b1 + 1;
+        }
+        logz_moments_kernel<<<batch, 256, 0, s>>>(
+            n, g.nsA, g.lanesA, g.lanesB, (const double *)(base + L.laneZA),
+            (const double *)(base + L.laneM1), (const double *)(base + L.laneZB), beta[j],
+            upstream, nbeta, j, grad, moment, nbeta * n * n, j * n * n);
+        L_CUDA(cudaGetLastError(), "log Z moments");
+    }
+    L_CUDA(cudaStreamSynchronize(s), "log Z backward");
+    return QBF_OK;
+}
+
+int danskin(const uint64_t *argmin_host, int n, int batch, const double *upstream, double *grad,
+            cudaStream_t s)
+{
+    if (!argmin_host || !grad)
+        return record_error(QBF_EINVAL, "null pointer argument");
+    if (n < 1 || n > 64 || batch < 1)
+        return record_error(QBF_EINVAL, "need 1 <= n <= 64 and batch >= 1");
+    std::lock_guard<std::mutex> lk(g_lmu);
+    char *base = nullptr;
+    int rc = lz_pool(al(sizeof(unsigned long long) * batch), &base);
+    if (rc)
+        return rc;
+    L_CUDA(cudaMemcpyAsync(base, argmin_host, sizeof(unsigned long long) * batch,
+                           cudaMemcpyHostToDevice, s),
+           "argmin upload");
+    danskin_kernel<<<batch, 256, 0, s>>>((const unsigned long long *)base, n, batch, upstream, grad);
+    L_CUDA(cudaGetLastError(), "danskin");
+    L_CUDA(cudaStreamSynchronize(s), "danskin");
+    return QBF_OK;
+}
+
+int release_logz()
+{
+    std::lock_guard<std::mutex> lk(g_lmu);
+    for (size_t d = 0; d < g_lpool.size(); ++d) {
+        if (!g_lpool[d].dev)
+            continue;
+        int cur = 0;
+        cudaGetDevice(&cur);
+        cudaSetDevice((int)d);
+        cudaDeviceSynchronize();
+        cudaFree(g_lpool[d].dev);
+        g_lpool[d] = LzPool();
+        cudaSetDevice(cur);
+    }
+    return QBF_OK;
+}
+
+}  // namespace qbf

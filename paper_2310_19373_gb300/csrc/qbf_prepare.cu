@@ -292,4 +292,108 @@ __global__ void __launch_bounds__(256) batched_tables_kernel(const BatchDesc *de
         tables_body(plan, d.ns, kRMax, recs + d.rec_off, nrec, K + i * 128, B);
 }
 
+// ---- Boltzmann log-partition: two-limb images ------------------------------
+//
+// For instance b and walk w (0: identity order, 1: variables rotated so that
+// walk variable v is the caller's variable (v + rot) mod n), writes two Plans:
+// hi = round(y * 2^sigma) and lo = round((y * 2^sigma - hi) * 2^16) for every
+// lin / S entry y.  Both limbs are exact int32 images (|lo| <= 2^15), so
+// hi * 2^16 + lo is the fixed-point value at scale 2^(sigma + 16), walked
+// exactly as two int32 walks in lockstep.  sigma comes from the unrotated
+// order so both walks share it.
+__global__ void __launch_bounds__(256) logz_prepare_kernel(const void *Q, int n, int dtype,
+                                                           int rot, Plan *plans)
+{
+    __shared__ double sQ[kMaxN * kMaxN];
+    __shared__ double redd[256];
+    __shared__ long long redl[256];
+    const int b = blockIdx.x >> 1, w = blockIdx.x & 1;
+    const int t = threadIdx.x;
+    const int nn = n * n;
+    const size_t esz = (dtype == QBF_F64) ? 8 : (dtype == QBF_I16 ? 2 : 4);
+    const void *Qb = (const char *)Q + (size_t)b * nn * esz;
+    Plan *hi = plans + (size_t)(b * 2 + w) * 2;
+    Plan *lo = hi + 1;
+    int bad = 0;
+    double vs = 0.0;
+    for (int e = t; e < nn; e += blockDim.x) {
+        const int i = e / n, j = e % n;
+        const double q = load_q(Qb, dtype, e);
+        if (!isfinite(q))
+            bad = 1;
+        if (i == j)
+            vs += fabs(q);
+        else if (i < j)
+            vs += fabs(q + load_q(Qb, dtype, j * n + i));
+        // rotated copy: walk variable (i', j') holds caller (i, j)
+        const int ri = w ? (i - rot + n) % n : i, rj = w ? (j - rot + n) % n : j;
+        sQ[ri * n + rj] = q;
+    }
+    bad = __syncthreads_or(bad);
+    if (bad) {
+        if (t == 0) {
+            hi->n = lo->n = n;
+            hi->status = lo->status = QBF_ENONFINITE;
+        }
+        return;
+    }
+    const double V_sym = block_sum_d(vs, redd);
+    int sigma = 0;
+    if (V_sym > 0.0) {
+        sigma = ilogb((2147483647.0 - (double)nn) / V_sym);
+        sigma = max(-1000, min(1000, sigma));
+    }
+    for (int iter = 0; iter < 64; ++iter) {
+        long long part = 0;
+        for (int e = t; e < nn; e += blockDim.x) {
+            const int i = e / n, j = e % n;
+            if (i > j)
+                continue;
+            const double y = (i == j) ? sQ[e] : sQ[e] + sQ[j * n + i];
+            part += llabs(__double2ll_rn(ldexp(y, sigma)));
+        }
+        if (block_sum_ll(part, redl) <= (long long)INT_MAX)
+            break;
+        --sigma;
+    }
+    for (int e = t; e < nn; e += blockDim.x) {
+        const int i = e / n, j = e % n;
+        const double y = (i == j) ? ldexp(sQ[e], sigma) : ldexp(sQ[e] + sQ[j * n + i], sigma);
+        const long long h = __double2ll_rn(y);
+        const long long l = __double2ll_rn(ldexp(y - (double)h, 16));
+        if (i == j) {
+            hi->lin[i] = (int)h;
+            lo->lin[i] = (int)l;
+            hi->S[e] = lo->S[e] = 0;
+        } else {
+            hi->S[e] = (int)h;
+            lo->S[e] = (int)l;
+        }
+    }
+    if (t == 0) {
+        hi->n = lo->n = n;
+        hi->dtype = lo->dtype = dtype;
+        hi->sigma = sigma;
+        lo->sigma = sigma + 16;
+        hi->window = lo->window = 0;
+        hi->status = lo->status = QBF_OK;
+    }
+}
+
+// Walk tables for every (instance, walk, limb) plan: block = plan index.
+__global__ void __launch_bounds__(256) logz_tables_kernel(const Plan *plans, int nsA, int nsB,
+                                                          Rec *recs, unsigned rec_stride, int *K)
+{
+    const int pi = blockIdx.x;           // (b * 2 + w) * 2 + limb
+    const int w = (pi >> 1) & 1;
+    const Plan *plan = plans + pi;
+    if (plan->status != QBF_OK)
+        return;
+    const int ns = w ? nsB : nsA;
+    const int R = min(kRMax, ns);
+    const unsigned nrec = 1u << (ns - R);
+    for (unsigned B = threadIdx.x; B < nrec; B += blockDim.x)
+        tables_body(plan, ns, R, recs + (size_t)pi * rec_stride, nrec, K + pi * 128, B);
+}
+
 }  // namespace qbf

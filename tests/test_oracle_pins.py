@@ -282,3 +282,20 @@ def test_planted_mistakes_are_caught():
     assert _pins_hold(good)
     for bad in (dropped_lower, swapped, wrong_sign):
         assert not _pins_hold(bad)
+
+
+def test_logz_moment_matches_central_differences():
+    """d log Z / d Q_ij = -beta E[x_i x_j]: the moment sums against differences of log Z (h = 1e-3)."""
+    n = 6
+    rng = np.random.default_rng(12)
+    Q = np.triu(rng.normal(0, 1 / np.sqrt(n), size=(n, n)))
+    h = 1e-3
+    for beta in (0.1, 1.0):
+        _, E, _, _ = oracle.logz(Q, [beta])
+        for i, j in [(0, 0), (1, 4), (2, 5), (5, 5), (3, 1)]:
+            Qp, Qm = Q.copy(), Q.copy()
+            Qp[i, j] += h
+            Qm[i, j] -= h
+            fd = (oracle.logz(Qp, [beta], moment=False)[0][0] -
+                  oracle.logz(Qm, [beta], moment=False)[0][0]) / (2 * h)
+            assert abs(fd - (-beta * E[0][i, j])) <= 1e-5 * max(1e-3, abs(beta * E[0][i, j]))
