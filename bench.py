@@ -150,7 +150,10 @@ def run_reference(args, rank):
     }), flush=True)
 
 
-def run_profile_case(n):
+VARIANTS = {"auto": 0, "split": 2, "tc": 3}
+
+
+def run_profile_case(n, variant=0):
     import torch
 
     import __graft_entry__
@@ -161,7 +164,7 @@ def run_profile_case(n):
 
     Q = torch.from_numpy(inputs.gaussian_f32(n, seed=0)).cuda()
     for _ in range(2):
-        sol = qb.solve(Q, timing=True)
+        sol = qb.solve(Q, timing=True, variant=variant)
     torch.cuda.synchronize()
     print(json.dumps({"profile_n": n, "min_value": sol.min_value, "argmin": sol.argmin,
                       "walk_ms": sol.walk_seconds * 1e3}))
@@ -243,6 +246,18 @@ def run_variants(dev, flush):
                                      "E[xx^T] for 3 betas",
                          "states": st, "forward_seconds": t_f, "backward_seconds": t_b,
                          "forward_states_per_s": st / t_f}
+    # the two kernel forms of the n = 40 headline solve, side by side
+    Q40 = torch.from_numpy(inputs.config_n40_f32(0)).to(dev)
+    for name, var in (("split_walk_n40", 2), ("tc_blocked_n40", 3)):
+        walk = []
+
+        def one(var=var, walk=walk):
+            walk.append(qb.solve(Q40, variant=var, timing=True).walk_seconds)
+
+        t = timed(one)
+        out[name] = {"workload": "n=40 FP32 (headline instance), certified min",
+                     "seconds": t, "states_per_s": 2.0 ** 40 / t,
+                     "min_kernel_ms": statistics.median(walk[1:]) * 1e3}
     # n = 32 int32 (dense), exact
     Q32 = torch.from_numpy(inputs.config_n32_int(0)).to(dev)
     t = timed(lambda: qb.solve(Q32))
@@ -285,6 +300,8 @@ def main():
     ap.add_argument("--profile-n", type=int, default=0,
                     help="profiling target: two solves of an n-variable Gaussian FP32 instance, "
                          "no timing (for ncu)")
+    ap.add_argument("--variant", default="auto", choices=["auto", "split", "tc"],
+                    help="kernel form of the headline solve (auto: the library's choice)")
     ap.add_argument("--alu-microbench", action="store_true",
                     help="print the ALU throughput table (roofline denominators) and exit")
     args = ap.parse_args()
@@ -298,7 +315,7 @@ def main():
         run_reference(args, rank)
         return
     if args.profile_n:
-        run_profile_case(args.profile_n)
+        run_profile_case(args.profile_n, VARIANTS[args.variant])
         return
     if args.alu_microbench:
         run_alu_microbench()
@@ -327,8 +344,9 @@ def main():
     flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)  # > 129 MB L2
     stream = torch.cuda.current_stream(dev)
 
+    variant = VARIANTS[args.variant]
     for _ in range(args.warmup):
-        qb.solve(Qd, timing=True)
+        qb.solve(Qd, timing=True, variant=variant)
     torch.cuda.synchronize(dev)
 
     clocks = ClockSampler(local)
@@ -344,7 +362,7 @@ def main():
         e0 = torch.cuda.Event(enable_timing=True)
         e1 = torch.cuda.Event(enable_timing=True)
         e0.record(stream)
-        sol = qb.solve(Qd, timing=True)
+        sol = qb.solve(Qd, timing=True, variant=variant)
         e1.record(stream)
         e1.synchronize()
         step_ms.append(e0.elapsed_time(e1))
@@ -369,7 +387,7 @@ def main():
         flush.zero_()
         torch.cuda.synchronize(dev)
         t0 = time.perf_counter()
-        qb.solve(Qh)
+        qb.solve(Qh, variant=variant)
         e2e_s.append(time.perf_counter() - t0)
     e2e_t = statistics.median(e2e_s)
     if pg:

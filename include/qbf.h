@@ -69,7 +69,9 @@ enum {
 enum {
     QBF_VARIANT_AUTO = 0,
     QBF_VARIANT_FIELD = 1, /* per-thread local-field vector g in registers  */
-    QBF_VARIANT_SPLIT = 2  /* field split into lane-invariant + lane parts  */
+    QBF_VARIANT_SPLIT = 2, /* field split into lane-invariant + lane parts  */
+    QBF_VARIANT_TC = 3     /* blocked form: cross term on tcgen05 tensor
+                              cores, tiles of 2^14 states (15 <= n <= 42)  */
 };
 
 typedef struct {
@@ -259,18 +261,29 @@ int qbf_walk_trace(const void *Q_dev, int n, int dtype, int prefix_bits, uint64_
                    int64_t *val_dev, int *sigma_out, void *stream);
 
 /*
- * qbf_prefix_minima -- the MIN walk alone, exposing its per-prefix minima.
+ * qbf_prefix_minima -- the MIN kernel alone, exposing its per-prefix minima.
  *
- * Runs the production MIN walk (the kernel that dominates qbf_solve) with
- * 2^prefix_bits threads over the whole space and writes, for every prefix p
- * (the top prefix_bits variables), the minimum over its 2^(n - prefix_bits)
- * suffix states of the fixed-point objective round(Q * 2^sigma) to
- * pmin_dev[p] (int32, 2^prefix_bits entries, caller-owned device memory).
- * *sigma_out receives sigma.  1 <= n <= 48, 0 <= prefix_bits <= min(n-1, 28).
- * Used to test the walk prefix by prefix against the oracle.
+ * Runs the production MIN kernel of `variant` (QBF_VARIANT_SPLIT / AUTO: the
+ * Gray walk with 2^prefix_bits threads; QBF_VARIANT_TC: the tensor-core blocked
+ * form, which requires prefix_bits = n - 14) over the whole space and writes,
+ * for every prefix p (the top prefix_bits variables), the minimum over its
+ * 2^(n - prefix_bits) suffix states of the fixed-point objective
+ * round(Q * 2^sigma) to pmin_dev[p] (int32, 2^prefix_bits entries,
+ * caller-owned device memory).  *sigma_out receives sigma.  1 <= n <= 48,
+ * 0 <= prefix_bits <= min(n-1, 28).  Used to test the kernels prefix by prefix
+ * against the oracle.
  */
-int qbf_prefix_minima(const void *Q_dev, int n, int dtype, int prefix_bits, int32_t *pmin_dev,
-                      int *sigma_out, void *stream);
+int qbf_prefix_minima(const void *Q_dev, int n, int dtype, int prefix_bits, int variant,
+                      int32_t *pmin_dev, int *sigma_out, void *stream);
+
+/*
+ * qbf_tc_selftest -- one tcgen05 MMA on given operands: D = A * B with A
+ * 128 x 16 and B 16 x 128 (row-major FP16 bit patterns, host memory) and D
+ * 128 x 128 FP32 (host).  Checks the shared-memory operand layout and the
+ * instruction descriptor the blocked form uses.  Allocates small device
+ * buffers and synchronises the device.
+ */
+int qbf_tc_selftest(const uint16_t *A_host, const uint16_t *B_host, float *D_host);
 
 /*
  * qbf_alu_microbench -- measures one ALU instruction class on every SM.

@@ -18,7 +18,7 @@ LIB_PATH = os.path.join(HERE, "_build", "libqubobf.so")
 QBF_F64, QBF_F32, QBF_I32, QBF_I16 = 0, 1, 2, 3
 QBF_OK, QBF_EINVAL, QBF_ENONFINITE, QBF_EDTYPE, QBF_ECUDA = 0, 1, 2, 3, 4
 QBF_EOVERFLOW, QBF_ECANCELED, QBF_ENOTIMPL, QBF_ERANGE = 5, 6, 7, 8
-QBF_VARIANT_AUTO, QBF_VARIANT_FIELD, QBF_VARIANT_SPLIT = 0, 1, 2
+QBF_VARIANT_AUTO, QBF_VARIANT_FIELD, QBF_VARIANT_SPLIT, QBF_VARIANT_TC = 0, 1, 2, 3
 QBF_MAX_N = 48
 QBF_MAX_TOPK = 64
 
@@ -98,8 +98,9 @@ _SIGS = {
                                          _VP]),
     "qbf_walk_trace": (ctypes.c_int, [_VP, ctypes.c_int, ctypes.c_int, ctypes.c_int, _VP, _VP,
                                       ctypes.POINTER(ctypes.c_int), _VP]),
-    "qbf_prefix_minima": (ctypes.c_int, [_VP, ctypes.c_int, ctypes.c_int, ctypes.c_int, _VP,
-                                         ctypes.POINTER(ctypes.c_int), _VP]),
+    "qbf_prefix_minima": (ctypes.c_int, [_VP, ctypes.c_int, ctypes.c_int, ctypes.c_int,
+                                         ctypes.c_int, _VP, ctypes.POINTER(ctypes.c_int), _VP]),
+    "qbf_tc_selftest": (ctypes.c_int, [_VP, _VP, _VP]),
     "qbf_alu_microbench": (ctypes.c_int, [ctypes.c_int, ctypes.POINTER(ctypes.c_double),
                                           ctypes.POINTER(ctypes.c_double),
                                           ctypes.POINTER(ctypes.c_double), _VP]),
@@ -249,13 +250,24 @@ def qbf_walk_trace(Q_dev: int, n: int, dtype: int, prefix_bits: int, idx_dev: in
     return sigma.value
 
 
-def qbf_prefix_minima(Q_dev: int, n: int, dtype: int, prefix_bits: int, pmin_dev: int,
-                      stream: int | None = None) -> int:
+def qbf_prefix_minima(Q_dev: int, n: int, dtype: int, prefix_bits: int, variant: int,
+                      pmin_dev: int, stream: int | None = None) -> int:
     sigma = ctypes.c_int()
-    rc = lib().qbf_prefix_minima(_VP(Q_dev), n, dtype, prefix_bits, _VP(pmin_dev),
+    rc = lib().qbf_prefix_minima(_VP(Q_dev), n, dtype, prefix_bits, variant, _VP(pmin_dev),
                                  ctypes.byref(sigma), _VP(stream or 0))
     _check(rc)
     return sigma.value
+
+
+def qbf_tc_selftest(A_fp16_bits, B_fp16_bits):
+    """A: 128x16, B: 16x128 uint16 arrays of FP16 bit patterns (numpy); returns D 128x128."""
+    import numpy as np
+
+    A = np.ascontiguousarray(A_fp16_bits, dtype=np.uint16)
+    B = np.ascontiguousarray(B_fp16_bits, dtype=np.uint16)
+    D = np.zeros((128, 128), dtype=np.float32)
+    _check(lib().qbf_tc_selftest(A.ctypes.data, B.ctypes.data, D.ctypes.data))
+    return D
 
 
 def qbf_alu_microbench(op: int, stream: int | None = None):
@@ -354,15 +366,16 @@ def solve(Q, top_k: int = 1, variant: int = QBF_VARIANT_AUTO, prefix_bits: int =
     return _solution(r)
 
 
-def prefix_minima(Q, prefix_bits: int):
-    """Per-prefix minima of the fixed-point objective from the MIN walk, and sigma."""
+def prefix_minima(Q, prefix_bits: int, variant: int = QBF_VARIANT_AUTO):
+    """Per-prefix minima of the fixed-point objective from the MIN kernel, and sigma."""
     import torch
 
     Q = Q.contiguous()
     n = Q.shape[0]
     pm = torch.empty(1 << prefix_bits, dtype=torch.int32, device=Q.device)
     s = torch.cuda.current_stream(Q.device).cuda_stream
-    sigma = qbf_prefix_minima(Q.data_ptr(), n, dtype_code(Q), prefix_bits, pm.data_ptr(), s)
+    sigma = qbf_prefix_minima(Q.data_ptr(), n, dtype_code(Q), prefix_bits, variant,
+                              pm.data_ptr(), s)
     return pm, sigma
 
 

@@ -16,6 +16,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <climits>
 #include <cstdio>
 #include <cstdlib>
 #include <cstring>
@@ -166,7 +167,14 @@ struct Geo {
 int plan_geometry(int n, const qbf_options &o, Geo *g)
 {
     int k;
-    if (o.prefix_bits >= 0) {
+    if (o.variant == QBF_VARIANT_TC) {
+        // tiles of 14 low bits are the prefixes of the certification step
+        if (n < kTcTileSuffixBits + 1 || n - kTcTileSuffixBits > 28)
+            return set_err(QBF_EINVAL, "the tensor-core form needs 15 <= n <= 42");
+        if (o.prefix_bits >= 0 && o.prefix_bits != n - kTcTileSuffixBits)
+            return set_err(QBF_EINVAL, "the tensor-core form fixes prefix_bits = n - 14");
+        k = n - kTcTileSuffixBits;
+    } else if (o.prefix_bits >= 0) {
         k = o.prefix_bits;
         if (k > n - 1 || k > 28)
             return set_err(QBF_EINVAL, "prefix_bits must be in [0, min(n-1, 28)]");
@@ -177,8 +185,11 @@ int plan_geometry(int n, const qbf_options &o, Geo *g)
         return set_err(QBF_EINVAL, "fix_bits must be in [0, n-1]");
     if (o.fix_bits > 0 && (o.fix_value >> o.fix_bits) != 0)
         return set_err(QBF_EINVAL, "fix_value has bits above fix_bits");
-    if (k < o.fix_bits)
+    if (k < o.fix_bits) {
+        if (o.variant == QBF_VARIANT_TC)
+            return set_err(QBF_EINVAL, "fix_bits must be <= n - 14 for the tensor-core form");
         k = o.fix_bits;
+    }
     g->n = n;
     g->k = k;
     g->ns = n - k;
@@ -206,10 +217,10 @@ int walk_grid(int R, int mode, int n, int ns, unsigned long long nitems)
 
 // Enqueue prepare + tables + constant-bank copy + counter reset.
 int enqueue_prepare(const void *Q, int n, int dtype, const Geo &g, char *base, const Layout &L,
-                    cudaStream_t s)
+                    cudaStream_t s, long long vmax = INT_MAX)
 {
     Plan *plan = (Plan *)(base + L.plan);
-    prepare_kernel<<<1, 256, 0, s>>>(Q, n, dtype, plan);
+    prepare_kernel<<<1, 256, 0, s>>>(Q, n, dtype, plan, vmax);
     QBF_CUDA(cudaGetLastError(), "prepare_kernel");
     const unsigned nrec = 1u << g.M;
     tables_kernel<<<(nrec + 255) / 256, 256, 0, s>>>(plan, g.ns, g.R, (Rec *)(base + L.recs), nrec,
@@ -246,11 +257,13 @@ int solve_locked(const void *Q, bool host_q, int n, int dtype, const qbf_options
         o.top_k = 1;
     if (o.top_k < 1 || o.top_k > QBF_MAX_TOPK)
         return set_err(QBF_EINVAL, "top_k must be in [1, 64]");
-    if (o.variant != QBF_VARIANT_AUTO && o.variant != QBF_VARIANT_SPLIT)
+    if (o.variant != QBF_VARIANT_AUTO && o.variant != QBF_VARIANT_SPLIT &&
+        o.variant != QBF_VARIANT_TC)
         return set_err(QBF_ENOTIMPL, "requested walk variant is not built");
     Geo g;
     if ((rc = plan_geometry(n, o, &g)))
         return rc;
+    const bool tc = (o.variant == QBF_VARIANT_TC);
 
     const unsigned long long npref = g.p_hi - g.p_lo;
     const size_t qbytes = host_q ? dtype_size(dtype) * n * n : 0;
@@ -265,7 +278,7 @@ int solve_locked(const void *Q, bool host_q, int n, int dtype, const qbf_options
                  "copy Q to device");
         Qdev = base + L.qcopy;
     }
-    if ((rc = enqueue_prepare(Qdev, n, dtype, g, base, L, s)))
+    if ((rc = enqueue_prepare(Qdev, n, dtype, g, base, L, s, tc ? kTcVmax : (long long)INT_MAX)))
         return rc;
 
     Plan *plan = (Plan *)(base + L.plan);
@@ -293,8 +306,12 @@ int solve_locked(const void *Q, bool host_q, int n, int dtype, const qbf_options
         QBF_CUDA(cudaEventCreate(&ev[1]), "cudaEventCreate");
         QBF_CUDA(cudaEventRecord(ev[0], s), "cudaEventRecord");
     }
-    QBF_CUDA(launch_walk(kModeMin, g.R, plan, recs, a, walk_grid(g.R, kModeMin, n, g.ns, a.nitems), s),
-             "walk (min)");
+    if (tc)
+        QBF_CUDA(launch_tc_min(plan, n, g.p_lo, g.p_hi, pmin, ctr, num_sms(), s), "tc (min)");
+    else
+        QBF_CUDA(launch_walk(kModeMin, g.R, plan, recs, a,
+                             walk_grid(g.R, kModeMin, n, g.ns, a.nitems), s),
+                 "walk (min)");
     if (o.timing)
         QBF_CUDA(cudaEventRecord(ev[1], s), "cudaEventRecord");
 
@@ -345,8 +362,15 @@ int solve_locked(const void *Q, bool host_q, int n, int dtype, const qbf_options
         if (PH->status == QBF_ENONFINITE)
             return set_err(QBF_ENONFINITE, "Q holds NaN or Inf");
         if (PH->status == QBF_ERANGE)
-            return set_err(QBF_ERANGE, "integer Q: sum |Q_ij| must stay below 2^31");
+            return set_err(QBF_ERANGE, tc ? "integer Q: the tensor-core form needs sum |Q_ij| < 2^22"
+                                          : "integer Q: sum |Q_ij| must stay below 2^31");
         return set_err(PH->status, "prepare failed");
+    }
+    {
+        int st = 0;
+        QBF_CUDA(cudaMemcpy(&st, &ctr->status, sizeof(int), cudaMemcpyDeviceToHost), "status");
+        if (st != QBF_OK)
+            return set_err(QBF_ECUDA, "a device-side wait ran out (tensor-core pipeline)");
     }
     if (R->status == QBF_EOVERFLOW)
         return set_err(QBF_EOVERFLOW, "more than 2^22 states inside the certification window");
@@ -366,7 +390,7 @@ int solve_locked(const void *Q, bool host_q, int n, int dtype, const qbf_options
     out->n_candidates = R->n_candidates;
     out->prefix_bits = g.k;
     out->suffix_bits = g.ns;
-    out->variant = QBF_VARIANT_SPLIT;
+    out->variant = tc ? QBF_VARIANT_TC : QBF_VARIANT_SPLIT;
     out->walk_launches = 1;
     // prepare, tables, reset, walk(min), threshold, flag, walk(emit), rescore, select
     out->kernel_launches = 9;
@@ -458,8 +482,8 @@ int qbf_walk_trace(const void *Q_dev, int n, int dtype, int prefix_bits, uint64_
     return QBF_OK;
 }
 
-int qbf_prefix_minima(const void *Q_dev, int n, int dtype, int prefix_bits, int32_t *pmin_dev,
-                      int *sigma_out, void *stream)
+int qbf_prefix_minima(const void *Q_dev, int n, int dtype, int prefix_bits, int variant,
+                      int32_t *pmin_dev, int *sigma_out, void *stream)
 {
     std::lock_guard<std::mutex> lk(g_mu);
     cudaStream_t s = (cudaStream_t)stream;
@@ -471,9 +495,13 @@ int qbf_prefix_minima(const void *Q_dev, int n, int dtype, int prefix_bits, int3
         return set_err(QBF_EDTYPE, "unknown dtype");
     if (prefix_bits < 0)
         return set_err(QBF_EINVAL, "prefix_bits must be given");
+    if (variant != QBF_VARIANT_AUTO && variant != QBF_VARIANT_SPLIT && variant != QBF_VARIANT_TC)
+        return set_err(QBF_ENOTIMPL, "requested walk variant is not built");
     qbf_options o;
     qbf_default_options(&o);
     o.prefix_bits = prefix_bits;
+    o.variant = variant;
+    const bool tc = (variant == QBF_VARIANT_TC);
     Geo g;
     int rc = plan_geometry(n, o, &g);
     if (rc)
@@ -483,7 +511,7 @@ int qbf_prefix_minima(const void *Q_dev, int n, int dtype, int prefix_bits, int3
     if ((rc = pool_get(L.total, sizeof(DevResult) + sizeof(Plan), &P)))
         return rc;
     char *base = (char *)P->dev;
-    if ((rc = enqueue_prepare(Q_dev, n, dtype, g, base, L, s)))
+    if ((rc = enqueue_prepare(Q_dev, n, dtype, g, base, L, s, tc ? kTcVmax : (long long)INT_MAX)))
         return rc;
     WalkArgs a;
     memset(&a, 0, sizeof(a));
@@ -495,9 +523,12 @@ int qbf_prefix_minima(const void *Q_dev, int n, int dtype, int prefix_bits, int3
     a.ctr = (Counters *)(base + L.ctr);
     a.pmin = pmin_dev;
     const Plan *plan = (const Plan *)(base + L.plan);
-    QBF_CUDA(launch_walk(kModeMin, g.R, plan, (const Rec *)(base + L.recs), a,
-                         walk_grid(g.R, kModeMin, n, g.ns, a.nitems), s),
-             "walk (min)");
+    if (tc)
+        QBF_CUDA(launch_tc_min(plan, n, g.p_lo, g.p_hi, pmin_dev, a.ctr, num_sms(), s), "tc (min)");
+    else
+        QBF_CUDA(launch_walk(kModeMin, g.R, plan, (const Rec *)(base + L.recs), a,
+                             walk_grid(g.R, kModeMin, n, g.ns, a.nitems), s),
+                 "walk (min)");
     char *h = (char *)P->host;
     QBF_CUDA(cudaMemcpyAsync(h, plan, offsetof(Plan, lin), cudaMemcpyDeviceToHost, s), "copy plan");
     QBF_CUDA(cudaStreamSynchronize(s), "prefix minima");
@@ -505,6 +536,20 @@ int qbf_prefix_minima(const void *Q_dev, int n, int dtype, int prefix_bits, int3
     if (PH->status != QBF_OK)
         return set_err(PH->status, "prepare failed");
     *sigma_out = PH->sigma;
+    return QBF_OK;
+}
+
+int qbf_tc_selftest(const uint16_t *A_host, const uint16_t *B_host, float *D_host)
+{
+    if (!A_host || !B_host || !D_host)
+        return set_err(QBF_EINVAL, "null pointer argument");
+    std::lock_guard<std::mutex> lk(g_mu);
+    int err = 0;
+    cudaError_t e = run_tc_selftest(A_host, B_host, D_host, &err);
+    if (e != cudaSuccess)
+        return cuda_err(e, "tensor-core self-test");
+    if (err)
+        return set_err(QBF_ECUDA, "tensor-core self-test: the MMA completion wait ran out");
     return QBF_OK;
 }
 

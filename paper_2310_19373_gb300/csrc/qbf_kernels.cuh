@@ -33,7 +33,7 @@ struct WalkArgs {
 };
 
 // qbf_prepare.cu
-__global__ void prepare_kernel(const void *Q, int n, int dtype, Plan *plan);
+__global__ void prepare_kernel(const void *Q, int n, int dtype, Plan *plan, long long vmax);
 __global__ void batched_prepare_kernel(const BatchDesc *desc, Plan *plans, int *status);
 __global__ void batched_tables_kernel(const BatchDesc *desc, const Plan *plans, Rec *recs, int *K);
 __global__ void logz_prepare_kernel(const void *Q, int n, int dtype, int rot, Plan *plans);
@@ -79,6 +79,14 @@ int logz_backward(const void *Q, int n, int dtype, int batch, const double *beta
 int danskin(const uint64_t *argmin_host, int n, int batch, const double *upstream, double *grad,
             cudaStream_t s);
 int release_logz();
+
+// qbf_tc.cu: tensor-core blocked form (tiles of 14 low bits)
+constexpr int kTcTileSuffixBits = 14;
+constexpr long long kTcVmax = (1ll << 22) - (1ll << 12);  // bound on sum |image| for exact FP32
+cudaError_t launch_tc_min(const Plan *plan, int n, unsigned long long p_lo,
+                          unsigned long long p_hi, int *pmin, Counters *ctr, int num_sms,
+                          cudaStream_t s);
+cudaError_t run_tc_selftest(const void *A_host, const void *B_host, float *D_host, int *err_host);
 
 // qbf_microbench.cu
 cudaError_t run_alu_microbench(int op, double *ops_per_clk_sm, double *sm_mhz, double *seconds,

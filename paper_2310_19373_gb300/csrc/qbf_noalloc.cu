@@ -184,7 +184,7 @@ int solve_noalloc_locked(const void *Q, int n, int dtype, const qbf_options *opt
     long long *vals = (long long *)(base + L.vals);
     DevResult *dres = (DevResult *)(base + L.res);
 
-    prepare_kernel<<<1, 256, 0, s>>>(Q, n, dtype, plan);
+    prepare_kernel<<<1, 256, 0, s>>>(Q, n, dtype, plan, (long long)INT_MAX);
     NA_CUDA(cudaGetLastError(), "prepare_kernel launch failed");
     const unsigned nrec = 1u << M;
     tables_kernel<<<(nrec + 255) / 256, 256, 0, s>>>(plan, ns, R, recs, nrec, Kbuf);

@@ -67,7 +67,8 @@ __device__ long long block_sum_ll(long long x, long long *red)
 // One CTA of 256 threads prepares one instance.  The walk dimension n may
 // exceed the caller's n_src: the extra variables get zero rows and columns
 // (used to give tiny instances of a batch the minimum walk width).
-__device__ void prepare_body(const void *Q, int n_src, int n, int dtype, Plan *plan)
+__device__ void prepare_body(const void *Q, int n_src, int n, int dtype, Plan *plan,
+                             long long vmax)
 {
     __shared__ double sQ[kMaxN * kMaxN];
     __shared__ double redd[256];
@@ -108,7 +109,7 @@ __device__ void prepare_body(const void *Q, int n_src, int n, int dtype, Plan *p
 
     int sigma = 0;
     if (!is_int && V_sym > 0.0) {
-        double room = (2147483647.0 - (double)nn) / V_sym;
+        double room = ((double)vmax - (double)nn) / V_sym;
         sigma = ilogb(room);  // floor(log2(room))
         if (sigma > 1000)
             sigma = 1000;
@@ -127,11 +128,11 @@ __device__ void prepare_body(const void *Q, int n_src, int n, int dtype, Plan *p
             part += llabs(__double2ll_rn(ldexp(x, sigma)));
         }
         vhat = block_sum_ll(part, redl);
-        if (vhat <= (long long)INT_MAX || is_int)
+        if (vhat <= vmax || is_int)
             break;
         --sigma;
     }
-    if (is_int && vhat > (long long)INT_MAX) {
+    if (is_int && vhat > vmax) {
         if (t == 0) {
             plan->n = n;
             plan->status = QBF_ERANGE;
@@ -187,9 +188,10 @@ __device__ void prepare_body(const void *Q, int n_src, int n, int dtype, Plan *p
     }
 }
 
-__global__ void __launch_bounds__(256) prepare_kernel(const void *Q, int n, int dtype, Plan *plan)
+__global__ void __launch_bounds__(256) prepare_kernel(const void *Q, int n, int dtype, Plan *plan,
+                                                      long long vmax)
 {
-    prepare_body(Q, n, n, dtype, plan);
+    prepare_body(Q, n, n, dtype, plan, vmax);
 }
 
 // Records and in-block corrections for a walk over suffix bits 0..ns-1 with
@@ -274,7 +276,7 @@ __global__ void __launch_bounds__(256) batched_prepare_kernel(const BatchDesc *d
 {
     const BatchDesc d = desc[blockIdx.x];
     Plan *plan = plans + blockIdx.x;
-    prepare_body(d.Q, d.n_src, d.n, d.dtype, plan);
+    prepare_body(d.Q, d.n_src, d.n, d.dtype, plan, (long long)INT_MAX);
     if (threadIdx.x == 0)
         status[blockIdx.x] = plan->status;
 }
