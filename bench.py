@@ -150,7 +150,7 @@ def run_reference(args, rank):
     }), flush=True)
 
 
-VARIANTS = {"auto": 0, "split": 2, "tc": 3}
+VARIANTS = {"auto": 0, "split": 2, "tc": 3, "f32": 4}
 
 
 def run_profile_case(n, variant=0):
@@ -300,7 +300,7 @@ def main():
     ap.add_argument("--profile-n", type=int, default=0,
                     help="profiling target: two solves of an n-variable Gaussian FP32 instance, "
                          "no timing (for ncu)")
-    ap.add_argument("--variant", default="auto", choices=["auto", "split", "tc"],
+    ap.add_argument("--variant", default="auto", choices=["auto", "split", "tc", "f32"],
                     help="kernel form of the headline solve (auto: the library's choice)")
     ap.add_argument("--alu-microbench", action="store_true",
                     help="print the ALU throughput table (roofline denominators) and exit")

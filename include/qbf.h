@@ -70,8 +70,10 @@ enum {
     QBF_VARIANT_AUTO = 0,
     QBF_VARIANT_FIELD = 1, /* per-thread local-field vector g in registers  */
     QBF_VARIANT_SPLIT = 2, /* field split into lane-invariant + lane parts  */
-    QBF_VARIANT_TC = 3     /* blocked form: cross term on tcgen05 tensor
+    QBF_VARIANT_TC = 3,    /* blocked form: cross term on tcgen05 tensor
                               cores, tiles of 2^14 states (15 <= n <= 42)  */
+    QBF_VARIANT_SPLIT_F32 = 4 /* split walk in packed FP32 on exact integers
+                                 (image < 2^23), two prefixes per thread     */
 };
 
 typedef struct {

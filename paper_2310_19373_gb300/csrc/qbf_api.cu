@@ -79,7 +79,7 @@ Layout make_layout(size_t nrec, size_t npref, size_t qbytes, bool need_cand)
     L.res = o;
     o = align256(o + sizeof(DevResult));
     L.kbuf = o;
-    o = align256(o + sizeof(int) * kKbufInts);
+    o = align256(o + sizeof(int) * kKbufInts + sizeof(unsigned long long) * 128);
     L.recs = o;
     o = align256(o + sizeof(Rec) * std::max<size_t>(nrec, 2));
     L.pmin = o;
@@ -161,6 +161,7 @@ int auto_suffix_bits(int n)
 
 struct Geo {
     int n, k, ns, R, M, q;
+    int ns_tab;  // suffix width the walk tables are built for
     unsigned long long p_lo, p_hi;
 };
 
@@ -174,6 +175,18 @@ int plan_geometry(int n, const qbf_options &o, Geo *g)
         if (o.prefix_bits >= 0 && o.prefix_bits != n - kTcTileSuffixBits)
             return set_err(QBF_EINVAL, "the tensor-core form fixes prefix_bits = n - 14");
         k = n - kTcTileSuffixBits;
+    } else if (o.variant == QBF_VARIANT_SPLIT_F32) {
+        // a lane walks nsw bits for both values of the pair bit (variable nsw)
+        if (n < 2)
+            return set_err(QBF_EINVAL, "the packed FP32 walk needs n >= 2");
+        if (o.prefix_bits >= 0) {
+            k = o.prefix_bits;
+            if (k > n - 2 || k > 28)
+                return set_err(QBF_EINVAL, "prefix_bits must be in [0, min(n-2, 28)] for the packed walk");
+        } else {
+            const int nsw = std::min(auto_suffix_bits(n), n - 1);
+            k = n - nsw - 1;
+        }
     } else if (o.prefix_bits >= 0) {
         k = o.prefix_bits;
         if (k > n - 1 || k > 28)
@@ -193,9 +206,18 @@ int plan_geometry(int n, const qbf_options &o, Geo *g)
     g->n = n;
     g->k = k;
     g->ns = n - k;
-    g->R = std::min(kRMax, g->ns);
-    g->M = g->ns - g->R;
-    g->q = std::min(g->M, 10);
+    if (o.variant == QBF_VARIANT_SPLIT_F32) {
+        const int nsw = g->ns - 1;
+        g->R = std::min(kRMax, nsw);
+        g->M = nsw - g->R;
+        g->q = std::min(g->ns - g->R, 10);
+        g->ns_tab = nsw;
+    } else {
+        g->R = std::min(kRMax, g->ns);
+        g->M = g->ns - g->R;
+        g->q = std::min(g->M, 10);
+        g->ns_tab = g->ns;
+    }
     if (o.fix_bits > 0) {
         g->p_lo = o.fix_value << (k - o.fix_bits);
         g->p_hi = (o.fix_value + 1) << (k - o.fix_bits);
@@ -223,8 +245,8 @@ int enqueue_prepare(const void *Q, int n, int dtype, const Geo &g, char *base, c
     prepare_kernel<<<1, 256, 0, s>>>(Q, n, dtype, plan, vmax);
     QBF_CUDA(cudaGetLastError(), "prepare_kernel");
     const unsigned nrec = 1u << g.M;
-    tables_kernel<<<(nrec + 255) / 256, 256, 0, s>>>(plan, g.ns, g.R, (Rec *)(base + L.recs), nrec,
-                                                    (int *)(base + L.kbuf));
+    tables_kernel<<<(nrec + 255) / 256, 256, 0, s>>>(plan, g.ns_tab, g.R, (Rec *)(base + L.recs),
+                                                    nrec, (int *)(base + L.kbuf));
     QBF_CUDA(cudaGetLastError(), "tables_kernel");
     QBF_CUDA(copy_corrections((const int *)(base + L.kbuf), s), "corrections to constant bank");
     reset_counters_kernel<<<1, 32, 0, s>>>((Counters *)(base + L.ctr));
@@ -258,12 +280,13 @@ int solve_locked(const void *Q, bool host_q, int n, int dtype, const qbf_options
     if (o.top_k < 1 || o.top_k > QBF_MAX_TOPK)
         return set_err(QBF_EINVAL, "top_k must be in [1, 64]");
     if (o.variant != QBF_VARIANT_AUTO && o.variant != QBF_VARIANT_SPLIT &&
-        o.variant != QBF_VARIANT_TC)
+        o.variant != QBF_VARIANT_TC && o.variant != QBF_VARIANT_SPLIT_F32)
         return set_err(QBF_ENOTIMPL, "requested walk variant is not built");
     Geo g;
     if ((rc = plan_geometry(n, o, &g)))
         return rc;
     const bool tc = (o.variant == QBF_VARIANT_TC);
+    const bool f32 = (o.variant == QBF_VARIANT_SPLIT_F32);
 
     const unsigned long long npref = g.p_hi - g.p_lo;
     const size_t qbytes = host_q ? dtype_size(dtype) * n * n : 0;
@@ -278,7 +301,8 @@ int solve_locked(const void *Q, bool host_q, int n, int dtype, const qbf_options
                  "copy Q to device");
         Qdev = base + L.qcopy;
     }
-    if ((rc = enqueue_prepare(Qdev, n, dtype, g, base, L, s, tc ? kTcVmax : (long long)INT_MAX)))
+    if ((rc = enqueue_prepare(Qdev, n, dtype, g, base, L, s,
+                              tc ? kTcVmax : (f32 ? kF32Vmax : (long long)INT_MAX))))
         return rc;
 
     Plan *plan = (Plan *)(base + L.plan);
@@ -308,6 +332,11 @@ int solve_locked(const void *Q, bool host_q, int n, int dtype, const qbf_options
     }
     if (tc)
         QBF_CUDA(launch_tc_min(plan, n, g.p_lo, g.p_hi, pmin, ctr, num_sms(), s), "tc (min)");
+    else if (f32)
+        QBF_CUDA(launch_walk_f32(g.R, plan, recs, a, (const int *)(base + L.kbuf),
+                                 (unsigned long long *)(base + L.kbuf + sizeof(int) * kKbufInts),
+                                 num_sms(), s),
+                 "walk f32 (min)");
     else
         QBF_CUDA(launch_walk(kModeMin, g.R, plan, recs, a,
                              walk_grid(g.R, kModeMin, n, g.ns, a.nitems), s),
@@ -362,8 +391,10 @@ int solve_locked(const void *Q, bool host_q, int n, int dtype, const qbf_options
         if (PH->status == QBF_ENONFINITE)
             return set_err(QBF_ENONFINITE, "Q holds NaN or Inf");
         if (PH->status == QBF_ERANGE)
-            return set_err(QBF_ERANGE, tc ? "integer Q: the tensor-core form needs sum |Q_ij| < 2^22"
-                                          : "integer Q: sum |Q_ij| must stay below 2^31");
+            return set_err(QBF_ERANGE,
+                           tc ? "integer Q: the tensor-core form needs sum |Q_ij| < 2^22"
+                              : (f32 ? "integer Q: the packed FP32 walk needs sum |Q_ij| < 2^23"
+                                     : "integer Q: sum |Q_ij| must stay below 2^31"));
         return set_err(PH->status, "prepare failed");
     }
     {
@@ -390,7 +421,7 @@ int solve_locked(const void *Q, bool host_q, int n, int dtype, const qbf_options
     out->n_candidates = R->n_candidates;
     out->prefix_bits = g.k;
     out->suffix_bits = g.ns;
-    out->variant = tc ? QBF_VARIANT_TC : QBF_VARIANT_SPLIT;
+    out->variant = tc ? QBF_VARIANT_TC : (f32 ? QBF_VARIANT_SPLIT_F32 : QBF_VARIANT_SPLIT);
     out->walk_launches = 1;
     // prepare, tables, reset, walk(min), threshold, flag, walk(emit), rescore, select
     out->kernel_launches = 9;
@@ -495,13 +526,15 @@ int qbf_prefix_minima(const void *Q_dev, int n, int dtype, int prefix_bits, int 
         return set_err(QBF_EDTYPE, "unknown dtype");
     if (prefix_bits < 0)
         return set_err(QBF_EINVAL, "prefix_bits must be given");
-    if (variant != QBF_VARIANT_AUTO && variant != QBF_VARIANT_SPLIT && variant != QBF_VARIANT_TC)
+    if (variant != QBF_VARIANT_AUTO && variant != QBF_VARIANT_SPLIT && variant != QBF_VARIANT_TC &&
+        variant != QBF_VARIANT_SPLIT_F32)
         return set_err(QBF_ENOTIMPL, "requested walk variant is not built");
     qbf_options o;
     qbf_default_options(&o);
     o.prefix_bits = prefix_bits;
     o.variant = variant;
     const bool tc = (variant == QBF_VARIANT_TC);
+    const bool f32 = (variant == QBF_VARIANT_SPLIT_F32);
     Geo g;
     int rc = plan_geometry(n, o, &g);
     if (rc)
@@ -511,7 +544,8 @@ int qbf_prefix_minima(const void *Q_dev, int n, int dtype, int prefix_bits, int 
     if ((rc = pool_get(L.total, sizeof(DevResult) + sizeof(Plan), &P)))
         return rc;
     char *base = (char *)P->dev;
-    if ((rc = enqueue_prepare(Q_dev, n, dtype, g, base, L, s, tc ? kTcVmax : (long long)INT_MAX)))
+    if ((rc = enqueue_prepare(Q_dev, n, dtype, g, base, L, s,
+                              tc ? kTcVmax : (f32 ? kF32Vmax : (long long)INT_MAX))))
         return rc;
     WalkArgs a;
     memset(&a, 0, sizeof(a));
@@ -525,6 +559,12 @@ int qbf_prefix_minima(const void *Q_dev, int n, int dtype, int prefix_bits, int 
     const Plan *plan = (const Plan *)(base + L.plan);
     if (tc)
         QBF_CUDA(launch_tc_min(plan, n, g.p_lo, g.p_hi, pmin_dev, a.ctr, num_sms(), s), "tc (min)");
+    else if (f32)
+        QBF_CUDA(launch_walk_f32(g.R, plan, (const Rec *)(base + L.recs), a,
+                                 (const int *)(base + L.kbuf),
+                                 (unsigned long long *)(base + L.kbuf + sizeof(int) * kKbufInts),
+                                 num_sms(), s),
+                 "walk f32 (min)");
     else
         QBF_CUDA(launch_walk(kModeMin, g.R, plan, (const Rec *)(base + L.recs), a,
                              walk_grid(g.R, kModeMin, n, g.ns, a.nitems), s),

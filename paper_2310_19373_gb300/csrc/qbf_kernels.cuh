@@ -80,6 +80,12 @@ int danskin(const uint64_t *argmin_host, int n, int batch, const double *upstrea
             cudaStream_t s);
 int release_logz();
 
+// qbf_walk_f32.cu: MIN walk in packed FP32 (image bounded by 2^23, pairs of prefixes)
+constexpr long long kF32Vmax = (1ll << 23) - (1ll << 12);
+cudaError_t launch_walk_f32(int R, const Plan *plan, const Rec *recs, const WalkArgs &a,
+                            const int *Kbuf_dev, unsigned long long *Kf2_dev, int num_sms,
+                            cudaStream_t s);
+
 // qbf_tc.cu: tensor-core blocked form (tiles of 14 low bits)
 constexpr int kTcTileSuffixBits = 14;
 constexpr long long kTcVmax = (1ll << 22) - (1ll << 12);  // bound on sum |image| for exact FP32

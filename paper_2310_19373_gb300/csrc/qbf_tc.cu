@@ -501,6 +501,7 @@ __global__ void __launch_bounds__(kTcThreads * kTcGroups, 1)
     group_sync(g);
 
     int Fp = 0, rowT = 0;  // F'(column t) and row t's constant for the current tile
+    int gm = INT_MAX;      // this group's minimum over its tiles (thread 0)
     for (int it = 0; ch < nchunks; ++it) {
         const unsigned long long ti = (ch << r) + (jt ^ (jt >> 1));
         unsigned long long nch = ch, njt = jt + 1;
@@ -597,11 +598,13 @@ __global__ void __launch_bounds__(kTcThreads * kTcGroups, 1)
             for (int i = 1; i < 4; ++i)
                 tm = min(tm, sh.wmin[g][i]);
             pmin[ti] = tm;
-            atomicMin(&ctr->gmin, tm);
+            gm = min(gm, tm);
         }
         ch = nch;
         jt = njt;
     }
+    if (t == 0 && gm != INT_MAX)
+        atomicMin(&ctr->gmin, gm);
     tc_fence_before();
     __syncthreads();
     if (tid < 32)
