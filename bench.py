@@ -34,7 +34,15 @@ WORKLOAD = ("single QUBO n=40, FP32 upper triangular, off-diagonal N(0,1), diago
 # bytes the end-to-end call moves per step: Q in (n*n*4) and the result out
 # (device result block: 64 doubles + 64 uint64 + 16 B, plus the 48-byte plan head)
 E2E_D2H_BYTES = 64 * 8 + 64 * 8 + 16 + 48
-ALGO_OPS_PER_STATE = 2  # one three-input add (new value) + one min per visited state
+# value operations the split walk retires per visited state: the new value is
+# the old one plus the lane part of the flipped variable's field plus the static
+# in-block correction (two adds), and it enters the running minimum (one min)
+ALGO_OPS_PER_STATE = 3
+# per SM and clock: 128 FP32 lanes (FADD / packed f32x2 add) and 128 INT32/ALU
+# lanes (IADD3, IMNMX, FMNMX and their three-input forms)
+PIPE_LANES_PER_SM = 128 + 128
+WALK_KERNELS = {0: "walk_split_kernel<6, MIN>", 2: "walk_split_kernel<6, MIN>",
+                3: "tc_min_kernel", 4: "walk_f32x2_min_kernel<6>"}
 
 
 def env_int(name, default):
@@ -120,6 +128,34 @@ def cpu_baseline(Q, target_s=12.0):
     return {"value": (1 << bits) / dt, "unit": "states/s", "cores": cores, "kind": "oracle",
             "sample": f"natural-order FP64 brute force over the first 2^{bits} states of the "
                       f"n=40 instance (top {N_VARS - bits} bits zero), {dt:.1f} s"}
+
+
+def init_ranks(world):
+    """torch.distributed over gloo for N > 1 replicas (host-side timing reduce
+    only: the path itself has no collective); None for one process."""
+    if world <= 1:
+        return None
+    import torch.distributed as dist
+
+    dist.init_process_group("gloo")
+    return dist
+
+
+def max_over_ranks(x, pg):
+    """The largest per-rank value over all ranks (the slowest replica sets the
+    time); x itself without a process group."""
+    if pg is None:
+        return float(x)
+    import torch
+
+    t = torch.tensor([float(x)], dtype=torch.float64)
+    pg.all_reduce(t, op=pg.ReduceOp.MAX)
+    return float(t.item())
+
+
+def replica_throughput(world, states_per_replica, seconds):
+    """Whole-job states/s: every rank walks its own full instance in `seconds`."""
+    return world * states_per_replica / seconds
 
 
 def run_reference(args, rank):
@@ -246,9 +282,9 @@ def run_variants(dev, flush):
                                      "E[xx^T] for 3 betas",
                          "states": st, "forward_seconds": t_f, "backward_seconds": t_b,
                          "forward_states_per_s": st / t_f}
-    # the two kernel forms of the n = 40 headline solve, side by side
+    # the three kernel forms of the n = 40 headline solve, side by side
     Q40 = torch.from_numpy(inputs.config_n40_f32(0)).to(dev)
-    for name, var in (("split_walk_n40", 2), ("tc_blocked_n40", 3)):
+    for name, var in (("packed_f32_walk_n40", 4), ("int32_walk_n40", 2), ("tc_blocked_n40", 3)):
         walk = []
 
         def one(var=var, walk=walk):
@@ -271,20 +307,21 @@ def run_variants(dev, flush):
     return out
 
 
-def load_traffic():
-    """DRAM traffic of the walk kernel from the committed ncu summary, if still current."""
+def load_traffic(kernel):
+    """DRAM bytes per launch of `kernel` from the committed ncu summary, if its
+    source file is unchanged since the counters were taken (else None)."""
     import hashlib
 
     path = os.path.join(ROOT, "profiles", "traffic.json")
     try:
         with open(path) as f:
-            t = json.load(f)
+            t = json.load(f)[kernel]
         src = os.path.join(ROOT, t["source"])
         h = hashlib.sha256(open(src, "rb").read()).hexdigest()
         if h != t["source_sha256"]:
             return None
         return t["bytes_per_full_launch"]
-    except (OSError, KeyError, ValueError):
+    except (OSError, KeyError, ValueError, TypeError):
         return None
 
 
@@ -330,12 +367,7 @@ def main():
     from paper_2310_19373_gb300 import _binding as qb
     from paper_2310_19373_gb300 import inputs
 
-    pg = None
-    if world > 1:
-        import torch.distributed as dist
-
-        dist.init_process_group("gloo")
-        pg = dist
+    pg = init_ranks(world)
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
     Qnp = inputs.config_n40_f32(0)
@@ -373,13 +405,9 @@ def main():
         pg.barrier()
     clk = clocks.stop()
 
-    ms = sum(step_ms) / len(step_ms)
-    if pg:
-        t = torch.tensor([ms], dtype=torch.float64)
-        pg.all_reduce(t, op=pg.ReduceOp.MAX)
-        ms = float(t.item())
+    ms = max_over_ranks(sum(step_ms) / len(step_ms), pg)
     states = float(1 << N_VARS)
-    value = world * states / (ms * 1e-3)
+    value = replica_throughput(world, states, ms * 1e-3)
 
     # end to end: Q from pinned host memory, result back to the host, every step
     e2e_s = []
@@ -389,24 +417,23 @@ def main():
         t0 = time.perf_counter()
         qb.solve(Qh, variant=variant)
         e2e_s.append(time.perf_counter() - t0)
-    e2e_t = statistics.median(e2e_s)
-    if pg:
-        t = torch.tensor([e2e_t], dtype=torch.float64)
-        pg.all_reduce(t, op=pg.ReduceOp.MAX)
-        e2e_t = float(t.item())
+    e2e_t = max_over_ranks(statistics.median(e2e_s), pg)
 
-    # roofline of the dominant kernel (the MIN walk): algorithmic lane-ops / device time
+    # roofline of the dominant kernel (the MIN walk): algorithmic value-ops / device time,
+    # against both 128-lane pipes of every SM at the maximum SM clock
     nsm = torch.cuda.get_device_properties(dev).multi_processor_count
     peaks = measured_peaks()
     fmax = float(peaks.get("sm_max_mhz", 2070.0))
-    peak_ops = nsm * 128 * fmax * 1e6
+    peak_ops = nsm * PIPE_LANES_PER_SM * fmax * 1e6
     walk_t = statistics.median(walk_s)
     achieved = ALGO_OPS_PER_STATE * states / walk_t
+    kernel = WALK_KERNELS.get(sol.variant, "walk")
+    path_dtype = "f32" if sol.variant == 4 else ("f16/f32" if sol.variant == 3 else "i32")
 
     line = {
         "metric": METRIC, "value": value, "unit": "states/s", "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
-        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "i32",
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": path_dtype,
         "data": "synthetic",
         "config": {"workload": WORKLOAD, "n": N_VARS, "top_k": 1,
                    "prefix_bits": sol.prefix_bits, "suffix_bits": sol.suffix_bits,
@@ -416,14 +443,16 @@ def main():
                    "n_candidates": sol.n_candidates, "error_bound": sol.error_bound,
                    "scale_bits": sol.scale_bits},
         "roofline": {"bound": "alu", "achieved": achieved / 1e12, "peak": peak_ops / 1e12,
-                     "unit": "Tlane-op/s", "frac": achieved / peak_ops,
-                     "traffic": load_traffic(), "kernel": "walk_split_kernel (MIN)",
+                     "unit": "Tvalue-op/s", "frac": achieved / peak_ops,
+                     "traffic": load_traffic(kernel), "kernel": kernel,
                      "kernel_ms": walk_t * 1e3,
-                     "peak_basis": f"{nsm} SMs x 128 lanes x {fmax:.0f} MHz",
+                     "peak_basis": (f"{nsm} SMs x (128 FP32 + 128 INT32/ALU lanes) x {fmax:.0f} MHz "
+                                    "(unit counts and clock; measured: FADD 126, IMNMX 127.5, "
+                                    "packed/three-input forms 127 values per clk per SM)"),
                      "ops_per_state": ALGO_OPS_PER_STATE,
                      "metric_normalised_ops_per_s": states * N_VARS / (ms * 1e-3),
                      "metric_normalised_frac": states * N_VARS / (ms * 1e-3) / peak_ops},
-        "e2e": {"value": world * states / e2e_t, "unit": "states/s",
+        "e2e": {"value": replica_throughput(world, states, e2e_t), "unit": "states/s",
                 "h2d_bytes_per_step": N_VARS * N_VARS * 4,
                 "d2h_bytes_per_step": E2E_D2H_BYTES},
         "gpu_launches": launches,

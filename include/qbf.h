@@ -67,7 +67,9 @@ enum {
 
 /* walk kernels */
 enum {
-    QBF_VARIANT_AUTO = 0,
+    QBF_VARIANT_AUTO = 0,  /* float Q, n >= 24: SPLIT_F32 (SPLIT if its wider
+                              certification window overflows the candidate
+                              buffer); otherwise SPLIT                      */
     QBF_VARIANT_FIELD = 1, /* per-thread local-field vector g in registers  */
     QBF_VARIANT_SPLIT = 2, /* field split into lane-invariant + lane parts  */
     QBF_VARIANT_TC = 3,    /* blocked form: cross term on tcgen05 tensor

@@ -265,8 +265,8 @@ int check_common(const void *Q, int n, int dtype, qbf_result *out)
     return QBF_OK;
 }
 
-int solve_locked(const void *Q, bool host_q, int n, int dtype, const qbf_options *opt_in,
-                 qbf_result *out, cudaStream_t s)
+int solve_one(const void *Q, bool host_q, int n, int dtype, const qbf_options *opt_in,
+              qbf_result *out, cudaStream_t s)
 {
     int rc = check_common(Q, n, dtype, out);
     if (rc)
@@ -424,9 +424,34 @@ int solve_locked(const void *Q, bool host_q, int n, int dtype, const qbf_options
     out->variant = tc ? QBF_VARIANT_TC : (f32 ? QBF_VARIANT_SPLIT_F32 : QBF_VARIANT_SPLIT);
     out->walk_launches = 1;
     // prepare, tables, reset, walk(min), threshold, flag, walk(emit), rescore, select
-    out->kernel_launches = 9;
+    // (+ the correction-pair conversion of the packed walk)
+    out->kernel_launches = f32 ? 10 : 9;
     out->walk_seconds = walk_ms * 1e-3;
     return QBF_OK;
+}
+
+// QBF_VARIANT_AUTO: float Q with n >= kAutoF32MinN takes the packed-FP32 walk
+// (faster on this part); its image is bounded by 2^23 instead of 2^31, so its
+// certification window is wider, and if that flags more candidates than the
+// candidate buffer holds the solve is repeated on the int32 walk.
+constexpr int kAutoF32MinN = 24;
+
+int solve_locked(const void *Q, bool host_q, int n, int dtype, const qbf_options *opt_in,
+                 qbf_result *out, cudaStream_t s)
+{
+    qbf_options o;
+    qbf_default_options(&o);
+    if (opt_in)
+        o = *opt_in;
+    if (o.variant == QBF_VARIANT_AUTO && (dtype == QBF_F64 || dtype == QBF_F32) &&
+        n >= kAutoF32MinN && o.prefix_bits <= n - 2) {
+        qbf_options of = o;
+        of.variant = QBF_VARIANT_SPLIT_F32;
+        const int rc = solve_one(Q, host_q, n, dtype, &of, out, s);
+        if (rc != QBF_EOVERFLOW)
+            return rc;
+    }
+    return solve_one(Q, host_q, n, dtype, &o, out, s);
 }
 
 }  // namespace

@@ -3,9 +3,9 @@
 // The walk is bound by integer/float ALU issue, not by HBM, so its roofline
 // denominator is the number of lane operations an SM retires per clock.
 // Each kernel below runs 8 independent dependency chains per thread of one
-// instruction class, fills every SM with one wave of resident blocks, and
-// times itself with the SM cycle counter.  The result is scalar lane
-// operations per SM clock per SM (a packed f32x2 add counts as two).
+// instruction class, fills every SM with one wave of resident blocks, and is
+// timed with CUDA events.  The result is lane operations per SM clock per SM
+// (a packed f32x2 add counts as two; each instruction of a pair counts one).
 #include <cstdint>
 #include <vector>
 
@@ -18,35 +18,23 @@ namespace {
 constexpr int kMbThreads = 512;
 constexpr int kRounds = 16;  // unrolled rounds per iteration, 8 chains each
 
-__device__ __forceinline__ float fmin3(float a, float b, float c)
-{
-    float r;
-    asm("min.f32 %0, %1, %2, %3;" : "=f"(r) : "f"(a), "f"(b), "f"(c));
-    return r;
-}
-
-__device__ __forceinline__ unsigned long long fadd2(unsigned long long a, unsigned long long b)
-{
-    unsigned long long r;
-    asm("add.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(a), "l"(b));
-    return r;
-}
-
 template <int OP>
 __global__ void __launch_bounds__(kMbThreads) alu_kernel(int iters, unsigned seed, unsigned *sink,
                                                          long long *cycles)
 {
-    unsigned a[8], m[8];
+    int x[8], y[8];
     float f[8], g[8];
     unsigned long long p[8];
+    const int ia = (int)(seed ^ threadIdx.x), ib = (int)(seed >> 3);
+    const float fa = 1.0f + (float)(threadIdx.x & 7) * 1e-7f, fb = 0.999f;
+    const unsigned long long pc = ((unsigned long long)__float_as_uint(fa) << 32) | __float_as_uint(fb);
     for (int j = 0; j < 8; ++j) {
-        a[j] = seed * (threadIdx.x + 1) + j * 7919u;
-        m[j] = a[j] ^ 0x5bd1e995u;
-        f[j] = (float)(a[j] & 0xffff) * 1e-3f;
+        x[j] = (int)(seed * (threadIdx.x + 1)) + j * 7919;
+        y[j] = x[j] ^ 0x5bd1e995;
+        f[j] = (float)(x[j] & 0xffff) * 1e-3f;
         g[j] = f[j] + 1.0f;
         p[j] = ((unsigned long long)__float_as_uint(f[j]) << 32) | __float_as_uint(g[j]);
     }
-    const float fs = (float)(seed & 0xff) * 1e-7f;
     __syncthreads();
     const long long t0 = clock64();
     for (int it = 0; it < iters; ++it) {
@@ -54,38 +42,31 @@ __global__ void __launch_bounds__(kMbThreads) alu_kernel(int iters, unsigned see
         for (int r = 0; r < kRounds; ++r) {
 #pragma unroll
             for (int j = 0; j < 8; ++j) {
-                const int j1 = (j + 1) & 7, j2 = (j + 2) & 7;
-                if constexpr (OP == 0) {
-                    a[j] = a[j] + a[j1] + seed;
-                } else if constexpr (OP == 1) {
-                    a[j] = (unsigned)min((int)a[j], (int)a[j1]);
-                } else if constexpr (OP == 2) {
-                    a[j] = (unsigned)__vimin3_s32((int)a[j], (int)a[j1], (int)a[j2]);
-                } else if constexpr (OP == 3) {
-                    f[j] = f[j] + f[j1];
-                } else if constexpr (OP == 4) {
-                    f[j] = fmaf(f[j], f[j1], fs);
-                } else if constexpr (OP == 5) {
-                    f[j] = fminf(f[j], f[j1]);
-                } else if constexpr (OP == 6) {
-                    f[j] = fmin3(f[j], f[j1], f[j2]);
-                } else if constexpr (OP == 7) {
-                    p[j] = fadd2(p[j], p[j1]);
-                } else if constexpr (OP == 8) {
-                    a[j] = a[j] + m[j1] + seed;
-                    m[j] = (unsigned)min((int)m[j], (int)a[j]);
-                } else {
-                    f[j] = f[j] + g[j1];
-                    g[j] = fminf(g[j], f[j]);
-                }
+                if constexpr (OP == 0 || OP == 8)
+                    asm volatile("{.reg .s32 t; add.s32 t, %0, %1; add.s32 %0, t, %2;}"
+                                 : "+r"(x[j]) : "r"(ia), "r"(ib));
+                if constexpr (OP == 1 || OP == 8)
+                    asm volatile("min.s32 %0, %0, %1;" : "+r"(y[j]) : "r"(ia));
+                if constexpr (OP == 2)
+                    x[j] = __vimin3_s32(x[j], ia, ib + j);
+                if constexpr (OP == 3 || OP == 9)
+                    asm volatile("add.rn.f32 %0, %0, %1;" : "+f"(f[j]) : "f"(fa));
+                if constexpr (OP == 4)
+                    asm volatile("fma.rn.f32 %0, %0, %1, %2;" : "+f"(f[j]) : "f"(fa), "f"(fb));
+                if constexpr (OP == 5 || OP == 9)
+                    asm volatile("min.f32 %0, %0, %1;" : "+f"(g[j]) : "f"(fa));
+                if constexpr (OP == 6)
+                    asm volatile("min.f32 %0, %0, %1, %2;" : "+f"(g[j]) : "f"(fa), "f"(fb));
+                if constexpr (OP == 7)
+                    asm volatile("add.rn.f32x2 %0, %0, %1;" : "+l"(p[j]) : "l"(pc));
             }
         }
     }
     const long long t1 = clock64();
     unsigned acc = 0;
     for (int j = 0; j < 8; ++j)
-        acc ^= a[j] ^ m[j] ^ __float_as_uint(f[j]) ^ __float_as_uint(g[j]) ^ (unsigned)p[j] ^
-               (unsigned)(p[j] >> 32);
+        acc ^= (unsigned)x[j] ^ (unsigned)y[j] ^ __float_as_uint(f[j]) ^ __float_as_uint(g[j]) ^
+               (unsigned)p[j] ^ (unsigned)(p[j] >> 32);
     if (acc == 0x12345678u)
         sink[0] = acc;
     if (threadIdx.x == 0)

@@ -10,9 +10,9 @@
 //     variable (the "pair bit", variable nsw), packed as (a, b) into one 64-bit
 //     register: one add.rn.f32x2 moves both.  The pair bit adds S[i][nsw] to
 //     the b half of every field and lin + its prefix field to the b value.
-// Per step: one packed add (the signed low-bit field pair), two scalar adds of
-// the static correction (a constant-bank operand) and one three-input min over
-// both halves.  The minimum is
+// Per step: two packed adds (the signed low-bit field pair, then the static
+// correction pair from the constant bank) and one three-input min over both
+// halves.  The minimum is
 // recorded per pair, i.e. per prefix of a walk with nsw + 1 suffix bits.
 #include <climits>
 
@@ -22,7 +22,7 @@
 
 namespace qbf {
 
-__constant__ float c_Kf[2][64];  // the static corrections K[parity][u] as FP32
+__constant__ unsigned long long c_K2[2][64];  // (K, K): the static corrections as FP32 pairs
 
 namespace {
 
@@ -70,14 +70,10 @@ __device__ __forceinline__ void block_f2(u64 &v, float &m, const u64 (&GL)[R])
         const int g = u ^ (u >> 1);
         const int nb = ((g >> l) & 1) ^ ((l == R - 1) ? PI : 0);
         v = nb ? f2add(v, GL[l]) : f2sub(v, GL[l]);
-        // the correction is the same for both halves: two scalar adds with a
-        // constant-bank operand cost less than materialising a (K, K) pair
+        v = f2add(v, c_K2[PI][u]);
         float lo, hi;
         f2unpack(v, lo, hi);
-        lo = __fadd_rn(lo, c_Kf[PI][u]);
-        hi = __fadd_rn(hi, c_Kf[PI][u]);
         m = fmin3f(m, lo, hi);
-        v = f2pack(lo, hi);
     }
 }
 
@@ -206,11 +202,13 @@ __global__ void __launch_bounds__(kWalkThreads) walk_f32x2_min_kernel(const Plan
     }
 }
 
-__global__ void k_float_kernel(const int *Kbuf, float *Kf)
+__global__ void k_pairs_kernel(const int *Kbuf, unsigned long long *Kf2)
 {
     const int e = threadIdx.x;
-    if (e < 128)
-        Kf[e] = (float)Kbuf[e];  // exact: |K| < 2^23
+    if (e < 128) {
+        const float k = (float)Kbuf[e];  // exact: |K| < 2^23
+        Kf2[e] = ((unsigned long long)__float_as_uint(k) << 32) | __float_as_uint(k);
+    }
 }
 
 size_t walk_f32_smem_bytes(int n, int nsp, int R)
@@ -249,12 +247,12 @@ cudaError_t launch_walk_f32(int R, const Plan *plan, const Rec *recs, const Walk
                             const int *Kbuf_dev, unsigned long long *Kf2_dev, int num_sms,
                             cudaStream_t s)
 {
-    float *Kf = reinterpret_cast<float *>(Kf2_dev);
-    k_float_kernel<<<1, 128, 0, s>>>(Kbuf_dev, Kf);
+    k_pairs_kernel<<<1, 128, 0, s>>>(Kbuf_dev, Kf2_dev);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess)
         return e;
-    e = cudaMemcpyToSymbolAsync(c_Kf, Kf, sizeof(float) * 128, 0, cudaMemcpyDeviceToDevice, s);
+    e = cudaMemcpyToSymbolAsync(c_K2, Kf2_dev, sizeof(unsigned long long) * 128, 0,
+                                cudaMemcpyDeviceToDevice, s);
     if (e != cudaSuccess)
         return e;
     switch (R) {
