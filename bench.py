@@ -42,7 +42,7 @@ ALGO_OPS_PER_STATE = 3
 # lanes (IADD3, IMNMX, FMNMX and their three-input forms)
 PIPE_LANES_PER_SM = 128 + 128
 WALK_KERNELS = {0: "walk_split_kernel<6, MIN>", 2: "walk_split_kernel<6, MIN>",
-                3: "tc_min_kernel", 4: "walk_f32x2_min_kernel<6>"}
+                3: "tc_min_kernel", 4: "walk_f32x2_min_kernel<6>", 5: "walk_mix_min_kernel<6>"}
 
 
 def env_int(name, default):
@@ -186,7 +186,7 @@ def run_reference(args, rank):
     }), flush=True)
 
 
-VARIANTS = {"auto": 0, "split": 2, "tc": 3, "f32": 4}
+VARIANTS = {"auto": 0, "split": 2, "tc": 3, "f32": 4, "mix": 5}
 
 
 def run_profile_case(n, variant=0):
@@ -282,9 +282,10 @@ def run_variants(dev, flush):
                                      "E[xx^T] for 3 betas",
                          "states": st, "forward_seconds": t_f, "backward_seconds": t_b,
                          "forward_states_per_s": st / t_f}
-    # the three kernel forms of the n = 40 headline solve, side by side
+    # the kernel forms of the n = 40 headline solve, side by side
     Q40 = torch.from_numpy(inputs.config_n40_f32(0)).to(dev)
-    for name, var in (("packed_f32_walk_n40", 4), ("int32_walk_n40", 2), ("tc_blocked_n40", 3)):
+    for name, var in (("two_pipe_walk_n40", 5), ("packed_f32_walk_n40", 4), ("int32_walk_n40", 2),
+                      ("tc_blocked_n40", 3)):
         walk = []
 
         def one(var=var, walk=walk):
@@ -337,7 +338,7 @@ def main():
     ap.add_argument("--profile-n", type=int, default=0,
                     help="profiling target: two solves of an n-variable Gaussian FP32 instance, "
                          "no timing (for ncu)")
-    ap.add_argument("--variant", default="auto", choices=["auto", "split", "tc", "f32"],
+    ap.add_argument("--variant", default="auto", choices=["auto", "split", "tc", "f32", "mix"],
                     help="kernel form of the headline solve (auto: the library's choice)")
     ap.add_argument("--alu-microbench", action="store_true",
                     help="print the ALU throughput table (roofline denominators) and exit")
@@ -428,7 +429,8 @@ def main():
     walk_t = statistics.median(walk_s)
     achieved = ALGO_OPS_PER_STATE * states / walk_t
     kernel = WALK_KERNELS.get(sol.variant, "walk")
-    path_dtype = "f32" if sol.variant == 4 else ("f16/f32" if sol.variant == 3 else "i32")
+    # arithmetic types of the MIN walk (all on exact integers; certification rescoring is FP64)
+    path_dtype = {3: "f16/f32", 4: "f32", 5: "f32+i32"}.get(sol.variant, "i32")
 
     line = {
         "metric": METRIC, "value": value, "unit": "states/s", "n_gpus": world,

@@ -175,6 +175,18 @@ int plan_geometry(int n, const qbf_options &o, Geo *g)
         if (o.prefix_bits >= 0 && o.prefix_bits != n - kTcTileSuffixBits)
             return set_err(QBF_EINVAL, "the tensor-core form fixes prefix_bits = n - 14");
         k = n - kTcTileSuffixBits;
+    } else if (o.variant == QBF_VARIANT_SPLIT_MIX) {
+        // a lane walks nsw bits for all eight values of the group bits nsw..nsw+2
+        if (n < 4)
+            return set_err(QBF_EINVAL, "the two-pipe walk needs n >= 4");
+        if (o.prefix_bits >= 0) {
+            k = o.prefix_bits;
+            if (k > n - 4 || k > 28)
+                return set_err(QBF_EINVAL, "prefix_bits must be in [0, min(n-4, 28)] for the two-pipe walk");
+        } else {
+            const int nsw = std::min(auto_suffix_bits(n), n - 3);
+            k = n - nsw - 3;
+        }
     } else if (o.variant == QBF_VARIANT_SPLIT_F32) {
         // a lane walks nsw bits for both values of the pair bit (variable nsw)
         if (n < 2)
@@ -206,7 +218,15 @@ int plan_geometry(int n, const qbf_options &o, Geo *g)
     g->n = n;
     g->k = k;
     g->ns = n - k;
-    if (o.variant == QBF_VARIANT_SPLIT_F32) {
+    if (o.variant == QBF_VARIANT_SPLIT_MIX) {
+        if (g->ns < 4)
+            return set_err(QBF_EINVAL, "fix_bits must be <= n - 4 for the two-pipe walk");
+        const int nsw = g->ns - 3;
+        g->R = std::min(kRMax, nsw);
+        g->M = nsw - g->R;
+        g->q = std::min(g->ns - g->R, 10);
+        g->ns_tab = nsw;
+    } else if (o.variant == QBF_VARIANT_SPLIT_F32) {
         const int nsw = g->ns - 1;
         g->R = std::min(kRMax, nsw);
         g->M = nsw - g->R;
@@ -280,13 +300,15 @@ int solve_one(const void *Q, bool host_q, int n, int dtype, const qbf_options *o
     if (o.top_k < 1 || o.top_k > QBF_MAX_TOPK)
         return set_err(QBF_EINVAL, "top_k must be in [1, 64]");
     if (o.variant != QBF_VARIANT_AUTO && o.variant != QBF_VARIANT_SPLIT &&
-        o.variant != QBF_VARIANT_TC && o.variant != QBF_VARIANT_SPLIT_F32)
+        o.variant != QBF_VARIANT_TC && o.variant != QBF_VARIANT_SPLIT_F32 &&
+        o.variant != QBF_VARIANT_SPLIT_MIX)
         return set_err(QBF_ENOTIMPL, "requested walk variant is not built");
     Geo g;
     if ((rc = plan_geometry(n, o, &g)))
         return rc;
     const bool tc = (o.variant == QBF_VARIANT_TC);
-    const bool f32 = (o.variant == QBF_VARIANT_SPLIT_F32);
+    const bool mix = (o.variant == QBF_VARIANT_SPLIT_MIX);
+    const bool f32 = (o.variant == QBF_VARIANT_SPLIT_F32) || mix;  // same image bound
 
     const unsigned long long npref = g.p_hi - g.p_lo;
     const size_t qbytes = host_q ? dtype_size(dtype) * n * n : 0;
@@ -332,6 +354,11 @@ int solve_one(const void *Q, bool host_q, int n, int dtype, const qbf_options *o
     }
     if (tc)
         QBF_CUDA(launch_tc_min(plan, n, g.p_lo, g.p_hi, pmin, ctr, num_sms(), s), "tc (min)");
+    else if (mix)
+        QBF_CUDA(launch_walk_mix(g.R, plan, recs, a, (const int *)(base + L.kbuf),
+                                 (unsigned long long *)(base + L.kbuf + sizeof(int) * kKbufInts),
+                                 num_sms(), s),
+                 "walk mix (min)");
     else if (f32)
         QBF_CUDA(launch_walk_f32(g.R, plan, recs, a, (const int *)(base + L.kbuf),
                                  (unsigned long long *)(base + L.kbuf + sizeof(int) * kKbufInts),
@@ -393,7 +420,7 @@ int solve_one(const void *Q, bool host_q, int n, int dtype, const qbf_options *o
         if (PH->status == QBF_ERANGE)
             return set_err(QBF_ERANGE,
                            tc ? "integer Q: the tensor-core form needs sum |Q_ij| < 2^22"
-                              : (f32 ? "integer Q: the packed FP32 walk needs sum |Q_ij| < 2^23"
+                              : (f32 ? "integer Q: the FP32-pipe walks need sum |Q_ij| < 2^23"
                                      : "integer Q: sum |Q_ij| must stay below 2^31"));
         return set_err(PH->status, "prepare failed");
     }
@@ -421,20 +448,23 @@ int solve_one(const void *Q, bool host_q, int n, int dtype, const qbf_options *o
     out->n_candidates = R->n_candidates;
     out->prefix_bits = g.k;
     out->suffix_bits = g.ns;
-    out->variant = tc ? QBF_VARIANT_TC : (f32 ? QBF_VARIANT_SPLIT_F32 : QBF_VARIANT_SPLIT);
+    out->variant = tc ? QBF_VARIANT_TC
+                      : (mix ? QBF_VARIANT_SPLIT_MIX : (f32 ? QBF_VARIANT_SPLIT_F32 : QBF_VARIANT_SPLIT));
     out->walk_launches = 1;
     // prepare, tables, reset, walk(min), threshold, flag, walk(emit), rescore, select
     // (+ the correction-pair conversion of the packed walk)
-    out->kernel_launches = f32 ? 10 : 9;
+    out->kernel_launches = f32 ? 10 : 9;  // the FP32-pipe walks convert the correction pairs
     out->walk_seconds = walk_ms * 1e-3;
     return QBF_OK;
 }
 
-// QBF_VARIANT_AUTO: float Q with n >= kAutoF32MinN takes the packed-FP32 walk
-// (faster on this part); its image is bounded by 2^23 instead of 2^31, so its
-// certification window is wider, and if that flags more candidates than the
-// candidate buffer holds the solve is repeated on the int32 walk.
-constexpr int kAutoF32MinN = 24;
+// QBF_VARIANT_AUTO with n >= kAutoMixMinN takes the two-pipe walk (the
+// fastest form on this part).  Its image is bounded by 2^23 instead of 2^31:
+// integer Q with a larger sum |Q_ij| is rejected by prepare (QBF_ERANGE)
+// before any walk work, and for float Q the certification window is 2^8
+// times wider, so if it flags more candidates than the candidate buffer holds
+// (QBF_EOVERFLOW) the solve is repeated on the int32 walk.
+constexpr int kAutoMixMinN = 24;
 
 int solve_locked(const void *Q, bool host_q, int n, int dtype, const qbf_options *opt_in,
                  qbf_result *out, cudaStream_t s)
@@ -443,12 +473,12 @@ int solve_locked(const void *Q, bool host_q, int n, int dtype, const qbf_options
     qbf_default_options(&o);
     if (opt_in)
         o = *opt_in;
-    if (o.variant == QBF_VARIANT_AUTO && (dtype == QBF_F64 || dtype == QBF_F32) &&
-        n >= kAutoF32MinN && o.prefix_bits <= n - 2) {
-        qbf_options of = o;
-        of.variant = QBF_VARIANT_SPLIT_F32;
-        const int rc = solve_one(Q, host_q, n, dtype, &of, out, s);
-        if (rc != QBF_EOVERFLOW)
+    if (o.variant == QBF_VARIANT_AUTO && n >= kAutoMixMinN && o.prefix_bits <= n - 4 &&
+        o.fix_bits <= n - 4) {
+        qbf_options om = o;
+        om.variant = QBF_VARIANT_SPLIT_MIX;
+        const int rc = solve_one(Q, host_q, n, dtype, &om, out, s);
+        if (rc != QBF_EOVERFLOW && rc != QBF_ERANGE)
             return rc;
     }
     return solve_one(Q, host_q, n, dtype, &o, out, s);
@@ -552,14 +582,15 @@ int qbf_prefix_minima(const void *Q_dev, int n, int dtype, int prefix_bits, int 
     if (prefix_bits < 0)
         return set_err(QBF_EINVAL, "prefix_bits must be given");
     if (variant != QBF_VARIANT_AUTO && variant != QBF_VARIANT_SPLIT && variant != QBF_VARIANT_TC &&
-        variant != QBF_VARIANT_SPLIT_F32)
+        variant != QBF_VARIANT_SPLIT_F32 && variant != QBF_VARIANT_SPLIT_MIX)
         return set_err(QBF_ENOTIMPL, "requested walk variant is not built");
     qbf_options o;
     qbf_default_options(&o);
     o.prefix_bits = prefix_bits;
     o.variant = variant;
     const bool tc = (variant == QBF_VARIANT_TC);
-    const bool f32 = (variant == QBF_VARIANT_SPLIT_F32);
+    const bool mix = (variant == QBF_VARIANT_SPLIT_MIX);
+    const bool f32 = (variant == QBF_VARIANT_SPLIT_F32) || mix;  // same image bound
     Geo g;
     int rc = plan_geometry(n, o, &g);
     if (rc)
@@ -584,6 +615,12 @@ int qbf_prefix_minima(const void *Q_dev, int n, int dtype, int prefix_bits, int 
     const Plan *plan = (const Plan *)(base + L.plan);
     if (tc)
         QBF_CUDA(launch_tc_min(plan, n, g.p_lo, g.p_hi, pmin_dev, a.ctr, num_sms(), s), "tc (min)");
+    else if (mix)
+        QBF_CUDA(launch_walk_mix(g.R, plan, (const Rec *)(base + L.recs), a,
+                                 (const int *)(base + L.kbuf),
+                                 (unsigned long long *)(base + L.kbuf + sizeof(int) * kKbufInts),
+                                 num_sms(), s),
+                 "walk mix (min)");
     else if (f32)
         QBF_CUDA(launch_walk_f32(g.R, plan, (const Rec *)(base + L.recs), a,
                                  (const int *)(base + L.kbuf),

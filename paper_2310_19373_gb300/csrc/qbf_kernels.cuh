@@ -82,6 +82,10 @@ int release_logz();
 
 // qbf_walk_f32.cu: MIN walk in packed FP32 (image bounded by 2^23, pairs of prefixes)
 constexpr long long kF32Vmax = (1ll << 23) - (1ll << 12);
+// qbf_walk_mix.cu: MIN walk on both pipes (same image bound; eight prefixes per thread)
+cudaError_t launch_walk_mix(int R, const Plan *plan, const Rec *recs, const WalkArgs &a,
+                            const int *Kbuf_dev, unsigned long long *Kf2_dev, int num_sms,
+                            cudaStream_t s);
 cudaError_t launch_walk_f32(int R, const Plan *plan, const Rec *recs, const WalkArgs &a,
                             const int *Kbuf_dev, unsigned long long *Kf2_dev, int num_sms,
                             cudaStream_t s);

@@ -19,6 +19,7 @@
 #include "qbf_internal.cuh"
 #include "qbf_kernels.cuh"
 #include "qbf_walk_core.cuh"
+#include "qbf_f32x2.cuh"
 
 namespace qbf {
 
@@ -26,40 +27,7 @@ __constant__ unsigned long long c_K2[2][64];  // (K, K): the static corrections 
 
 namespace {
 
-typedef unsigned long long u64;
-
-__device__ __forceinline__ u64 f2add(u64 a, u64 b)
-{
-    u64 r;
-    asm("add.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(a), "l"(b));
-    return r;
-}
-
-__device__ __forceinline__ u64 f2sub(u64 a, u64 b)
-{
-    u64 r;
-    asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(a), "l"(b));
-    return r;
-}
-
-__device__ __forceinline__ u64 f2pack(float lo, float hi)
-{
-    u64 r;
-    asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(lo), "f"(hi));
-    return r;
-}
-
-__device__ __forceinline__ void f2unpack(u64 v, float &lo, float &hi)
-{
-    asm("mov.b64 {%0, %1}, %2;" : "=f"(lo), "=f"(hi) : "l"(v));
-}
-
-__device__ __forceinline__ float fmin3f(float a, float b, float c)
-{
-    float r;
-    asm("min.f32 %0, %1, %2, %3;" : "=f"(r) : "f"(a), "f"(b), "f"(c));
-    return r;
-}
+using f32x2::u64;
 
 template <int R, int PI>
 __device__ __forceinline__ void block_f2(u64 &v, float &m, const u64 (&GL)[R])
@@ -69,11 +37,11 @@ __device__ __forceinline__ void block_f2(u64 &v, float &m, const u64 (&GL)[R])
         const int l = ctz_c(u);
         const int g = u ^ (u >> 1);
         const int nb = ((g >> l) & 1) ^ ((l == R - 1) ? PI : 0);
-        v = nb ? f2add(v, GL[l]) : f2sub(v, GL[l]);
-        v = f2add(v, c_K2[PI][u]);
+        v = nb ? f32x2::add(v, GL[l]) : f32x2::sub(v, GL[l]);
+        v = f32x2::add(v, c_K2[PI][u]);
         float lo, hi;
-        f2unpack(v, lo, hi);
-        m = fmin3f(m, lo, hi);
+        f32x2::unpack(v, lo, hi);
+        m = f32x2::min3(m, lo, hi);
     }
 }
 
@@ -82,16 +50,16 @@ __device__ __forceinline__ void trans_f2(u64 &v, float &m, u64 (&GL)[R], const i
                                          const int4 rb, const u64 *sC2, int stride, int slot)
 {
     const float T = (float)ra.x;
-    v = f2add(v, f2pack(T, T));
-    v = f2add(v, sC2[ra.y * stride + slot]);
+    v = f32x2::add(v, f32x2::pack(T, T));
+    v = f32x2::add(v, sC2[ra.y * stride + slot]);
     float lo, hi;
-    f2unpack(v, lo, hi);
-    m = fmin3f(m, lo, hi);
+    f32x2::unpack(v, lo, hi);
+    m = f32x2::min3(m, lo, hi);
     const int W[6] = {ra.z, ra.w, rb.x, rb.y, rb.z, rb.w};
 #pragma unroll
     for (int i = 0; i < R; ++i) {
         const float w = (float)W[i];
-        GL[i] = f2add(GL[i], f2pack(w, w));
+        GL[i] = f32x2::add(GL[i], f32x2::pack(w, w));
     }
 }
 
@@ -161,7 +129,7 @@ __global__ void __launch_bounds__(kWalkThreads) walk_f32x2_min_kernel(const Plan
             for (int j = 0; j < kp; ++j)
                 if ((p >> j) & 1)
                     c += sS[ii * n + nsp + j];
-            GL[ii] = f2pack((float)c, (float)(c + sS[ii * n + nsw]));
+            GL[ii] = f32x2::pack((float)c, (float)(c + sS[ii * n + nsw]));
         }
         for (int ii = R; ii < nsw; ++ii) {
             int c = 0;
@@ -169,10 +137,10 @@ __global__ void __launch_bounds__(kWalkThreads) walk_f32x2_min_kernel(const Plan
                 if ((p >> j) & 1)
                     c += sS[ii * n + nsp + j];
             const int cb = c + sS[ii * n + nsw];
-            sC2[(2 * (ii - R) + 1) * stride + slot] = f2pack((float)c, (float)cb);
-            sC2[(2 * (ii - R)) * stride + slot] = f2pack((float)-c, (float)-cb);
+            sC2[(2 * (ii - R) + 1) * stride + slot] = f32x2::pack((float)c, (float)cb);
+            sC2[(2 * (ii - R)) * stride + slot] = f32x2::pack((float)-c, (float)-cb);
         }
-        u64 v = f2pack((float)va, (float)vb);
+        u64 v = f32x2::pack((float)va, (float)vb);
         float m = fminf((float)va, (float)vb);
         if (M == 0) {
             block_f2<R, 0>(v, m, GL);

@@ -76,37 +76,3 @@ def test_f32_workloads():
         s = qb.solve(dev(Q), fix_bits=20, fix_value=fv, variant=F32)
         assert (s.min_value, s.argmin) == oracle.brute_min(Q, fv << 20, (fv + 1) << 20)
 
-
-def test_auto_takes_packed_walk_for_float_q():
-    """AUTO: float Q with n >= 24 runs the packed walk, integer Q the int32 walk."""
-    n = 26
-    rng = np.random.default_rng(26)
-    Qf = np.triu(rng.normal(size=(n, n))).astype(np.float32)
-    sol = qb.solve(dev(Qf))
-    assert sol.variant == F32
-    assert (sol.min_value, sol.argmin) == oracle.brute_min(Qf)
-    Qi = np.triu(rng.integers(-50, 51, size=(n, n))).astype(np.int32)
-    sol = qb.solve(dev(Qi))
-    assert sol.variant == qb.QBF_VARIANT_SPLIT
-    assert (int(sol.min_value), sol.argmin) == tuple(int(v) for v in oracle.brute_min(Qi))
-
-
-def test_auto_falls_back_when_packed_window_overflows():
-    """One dominant entry sets the scale.  The small diagonal terms (about 0.2
-    quanta of the 2^23-bounded image) round to zero there, so all 2^25 states
-    with x_0 = 1 tie inside the packed walk's certification window, more
-    candidates than the buffer holds.  In the 2^31-bounded image of the int32
-    walk they are about 55 quanta each, so AUTO repeats the solve there and
-    still returns the exact optimum."""
-    n = 26
-    Q = np.zeros((n, n))
-    Q[0, 0] = -1.0
-    for i in range(1, n):
-        Q[i, i] = -5e-8 * (1.0 + i / 100.0)
-    with pytest.raises(qb.QbfError) as e:
-        qb.solve(dev(Q), variant=F32)
-    assert e.value.status == qb.QBF_EOVERFLOW
-    sol = qb.solve(dev(Q))
-    assert sol.variant == qb.QBF_VARIANT_SPLIT
-    assert sol.argmin == (1 << n) - 1
-    assert (sol.min_value, sol.argmin) == oracle.brute_min(Q)
