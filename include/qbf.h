@@ -148,6 +148,31 @@ int qbf_solve_host(const void *Q_host, int n, int dtype, const qbf_options *opt,
                    qbf_result *out, void *stream);
 
 /*
+ * qbf_solve_ising -- ground state of an Ising energy by the same solver.
+ *
+ * The introduction (Section 1) motivates QUBO by its equivalence with the
+ * Ising model.  For spins s_i in {-1, +1} this call minimises
+ *     E(s) = s^T J s + h^T s = sum_ij J_ij s_i s_j + sum_i h_i s_i
+ * (every entry of J counts; the diagonal adds the constant sum_i J_ii).  With
+ * s = 2x - 1, E(s) = x^T Q x + c for Q = 4J + diag(2h - 2R - 2C) (R, C: row
+ * and column sums of J) and c = sum_ij J_ij - sum_i h_i; the call builds Q on
+ * the device and runs qbf_solve on it.
+ *
+ * J_dev : device pointer, n*n elements of `dtype`, row-major.  Read only.
+ * h_dev : device pointer, n elements of `dtype`.  Read only.
+ * out   : as qbf_solve, with values E(s) (= f_Q + c) and indices whose bit i
+ *         is 1 iff s_i = +1; ties go to the lowest such index.  Float J, h:
+ *         Q is formed in FP64 (its diagonal with one rounding per term) and
+ *         c is added in FP64, so the values carry those roundings on top of
+ *         the certified f_Q.  Integer J, h: exact; QBF_ERANGE if an entry of
+ *         Q leaves int32.
+ * Uses a fixed device buffer of the library (no allocation beyond
+ * qbf_solve's); synchronises `stream` before returning.
+ */
+int qbf_solve_ising(const void *J_dev, const void *h_dev, int n, int dtype,
+                    const qbf_options *opt, qbf_result *out, void *stream);
+
+/*
  * qbf_solve_batched -- minimum and lowest-index argmin of many independent QUBOs.
  *
  * Section 3.1's prefix split applied across instances: the prefixes of all

@@ -78,6 +78,8 @@ _SIGS = {
                                  ctypes.POINTER(QbfResult), _VP]),
     "qbf_solve_host": (ctypes.c_int, [_VP, ctypes.c_int, ctypes.c_int,
                                       ctypes.POINTER(QbfOptions), ctypes.POINTER(QbfResult), _VP]),
+    "qbf_solve_ising": (ctypes.c_int, [_VP, _VP, ctypes.c_int, ctypes.c_int,
+                                       ctypes.POINTER(QbfOptions), ctypes.POINTER(QbfResult), _VP]),
     "qbf_solve_batched": (ctypes.c_int, [ctypes.POINTER(ctypes.c_void_p), ctypes.POINTER(ctypes.c_int),
                                          ctypes.POINTER(ctypes.c_int), ctypes.c_int,
                                          ctypes.POINTER(QbfOptions), ctypes.POINTER(ctypes.c_double),
@@ -157,6 +159,16 @@ def qbf_solve_host(Q_host: int, n: int, dtype: int, opt: QbfOptions | None,
     rc = lib().qbf_solve_host(_VP(Q_host), n, dtype,
                               ctypes.byref(opt) if opt is not None else None,
                               ctypes.byref(out), _VP(stream or 0))
+    _check(rc)
+    return out
+
+
+def qbf_solve_ising(J_dev: int, h_dev: int, n: int, dtype: int, opt: QbfOptions | None,
+                    stream: int | None = None):
+    out = QbfResult()
+    rc = lib().qbf_solve_ising(_VP(J_dev), _VP(h_dev), n, dtype,
+                               ctypes.byref(opt) if opt is not None else None,
+                               ctypes.byref(out), _VP(stream or 0))
     _check(rc)
     return out
 
@@ -327,6 +339,10 @@ class Solution:
         """argmin as a 0/1 list, x_i = bit i of the natural index."""
         return [(self.argmin >> i) & 1 for i in range(n)]
 
+    def spins(self, n: int):
+        """argmin of an Ising solve as spins, s_i = 2 x_i - 1."""
+        return [2 * b - 1 for b in self.x(n)]
+
 
 def _solution(r: QbfResult) -> Solution:
     k = r.top_k
@@ -365,6 +381,24 @@ def solve(Q, top_k: int = 1, variant: int = QBF_VARIANT_AUTO, prefix_bits: int =
     else:
         s = stream if stream is not None else torch.cuda.current_stream().cuda_stream
         r = qbf_solve_host(Q.data_ptr(), n, dtype_code(Q), opt, s)
+    return _solution(r)
+
+
+def solve_ising(J, h, top_k: int = 1, variant: int = QBF_VARIANT_AUTO, stream=None) -> Solution:
+    """Minimise E(s) = s^T J s + h^T s over s in {-1, +1}^n for CUDA tensors J
+    (n x n) and h (n) of one dtype; indices have bit i = 1 iff s_i = +1
+    (Solution.spins turns one into the spin vector)."""
+    import torch
+
+    if J.dim() != 2 or J.shape[0] != J.shape[1] or h.shape != (J.shape[0],):
+        raise QbfError(QBF_EINVAL, "J must be n x n and h of length n")
+    if J.dtype != h.dtype or not (J.is_cuda and h.is_cuda):
+        raise QbfError(QBF_EINVAL, "J and h must be CUDA tensors of one dtype")
+    J, h = J.contiguous(), h.contiguous()
+    opt = make_options(top_k, variant, -1, 0, 0, False)
+    s = stream if stream is not None else torch.cuda.current_stream(J.device).cuda_stream
+    with torch.cuda.device(J.device):
+        r = qbf_solve_ising(J.data_ptr(), h.data_ptr(), J.shape[0], dtype_code(J), opt, s)
     return _solution(r)
 
 

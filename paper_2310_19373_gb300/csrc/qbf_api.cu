@@ -518,6 +518,32 @@ int qbf_solve_host(const void *Q_host, int n, int dtype, const qbf_options *opt,
     return solve_locked(Q_host, true, n, dtype, opt, out, (cudaStream_t)stream);
 }
 
+int qbf_solve_ising(const void *J_dev, const void *h_dev, int n, int dtype,
+                    const qbf_options *opt, qbf_result *out, void *stream)
+{
+    std::lock_guard<std::mutex> lk(g_mu);
+    cudaStream_t s = (cudaStream_t)stream;
+    if (!J_dev || !h_dev || !out)
+        return set_err(QBF_EINVAL, "null pointer argument");
+    if (n < 1 || n > QBF_MAX_N)
+        return set_err(QBF_EINVAL, "n must be in [1, 48]");
+    if (dtype_size(dtype) == 0)
+        return set_err(QBF_EDTYPE, "unknown dtype");
+    const void *Q = nullptr;
+    int qdtype = 0, st = QBF_OK;
+    double c = 0.0;
+    QBF_CUDA(ising_to_qubo(J_dev, h_dev, n, dtype, &Q, &qdtype, &c, &st, s), "ising to qubo");
+    if (st != QBF_OK)
+        return set_err(QBF_ERANGE, "integer J, h: an entry of 4J + diag(2h - 2R - 2C) leaves int32");
+    const int rc = solve_locked(Q, false, n, qdtype, opt, out, s);
+    if (rc)
+        return rc;
+    out->min_value += c;
+    for (int i = 0; i < out->top_k; ++i)
+        out->topk_value[i] += c;
+    return QBF_OK;
+}
+
 int qbf_walk_trace(const void *Q_dev, int n, int dtype, int prefix_bits, uint64_t *idx_dev,
                    int64_t *val_dev, int *sigma_out, void *stream)
 {

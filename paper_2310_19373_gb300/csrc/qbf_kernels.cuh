@@ -82,6 +82,12 @@ int release_logz();
 
 // qbf_walk_f32.cu: MIN walk in packed FP32 (image bounded by 2^23, pairs of prefixes)
 constexpr long long kF32Vmax = (1ll << 23) - (1ll << 12);
+// qbf_ising.cu: Q = 4J + diag(2h - 2R - 2C) and c into a fixed device buffer
+// (FP64 Q for float J, h; int32 Q for integer J, h); returns Q, its dtype, c
+// and the range status on the host after synchronising s
+cudaError_t ising_to_qubo(const void *J, const void *h, int n, int dtype, const void **Q,
+                          int *qdtype, double *c_host, int *status_host, cudaStream_t s);
+
 // qbf_walk_mix.cu: MIN walk on both pipes (same image bound; eight prefixes per thread)
 cudaError_t launch_walk_mix(int R, const Plan *plan, const Rec *recs, const WalkArgs &a,
                             const int *Kbuf_dev, unsigned long long *Kf2_dev, int num_sms,
