@@ -41,7 +41,8 @@ ALGO_OPS_PER_STATE = 3
 # per SM and clock: 128 FP32 lanes (FADD / packed f32x2 add) and 128 INT32/ALU
 # lanes (IADD3, IMNMX, FMNMX and their three-input forms)
 PIPE_LANES_PER_SM = 128 + 128
-WALK_KERNELS = {0: "walk_split_kernel<6, MIN>", 2: "walk_split_kernel<6, MIN>",
+WALK_KERNELS = {0: "walk_split_kernel<6, MIN>", 1: "field_min_kernel", 2: "walk_split_kernel<6, MIN>",
+                6: "naive_min_kernel",
                 3: "tc_min_kernel", 4: "walk_f32x2_min_kernel<6>", 5: "walk_mix_min_kernel<6>"}
 
 
@@ -186,7 +187,7 @@ def run_reference(args, rank):
     }), flush=True)
 
 
-VARIANTS = {"auto": 0, "split": 2, "tc": 3, "f32": 4, "mix": 5}
+VARIANTS = {"auto": 0, "field": 1, "split": 2, "tc": 3, "f32": 4, "mix": 5, "naive": 6}
 
 
 def run_profile_case(n, variant=0):
@@ -295,6 +296,25 @@ def run_variants(dev, flush):
         out[name] = {"workload": "n=40 FP32 (headline instance), certified min",
                      "seconds": t, "states_per_s": 2.0 ** 40 / t,
                      "min_kernel_ms": statistics.median(walk[1:]) * 1e3}
+    # the paper's comparison on this GPU (MIN kernel times, one n = 32 FP32 instance):
+    # naive O(n^2) evaluation per state, the plain Gray walk (n_s + 1 adds per state,
+    # Algorithm 1), and the split walks of this library
+    Qg = torch.from_numpy(inputs.gaussian_f32(32, seed=0)).to(dev)
+    forms = {}
+    for name, var in (("naive", 6), ("gray_field", 1), ("int32_split", 2), ("two_pipe", 5)):
+        walk = []
+
+        def one(var=var, walk=walk):
+            walk.append(qb.solve(Qg, variant=var, timing=True).walk_seconds)
+
+        t = timed(one, reps=2)
+        kms = statistics.median(walk[1:]) * 1e3
+        forms[name] = {"seconds": t, "min_kernel_ms": kms, "states_per_s": 2.0 ** 32 / (kms * 1e-3)}
+    out["naive_vs_gray_n32"] = {
+        "workload": "n=32 FP32 off-diagonal N(0,1), diagonal N(-0.5,1), seed 0; certified min",
+        "forms": forms,
+        "gray_over_naive": forms["naive"]["min_kernel_ms"] / forms["gray_field"]["min_kernel_ms"],
+        "two_pipe_over_gray": forms["gray_field"]["min_kernel_ms"] / forms["two_pipe"]["min_kernel_ms"]}
     # n = 32 int32 (dense), exact
     Q32 = torch.from_numpy(inputs.config_n32_int(0)).to(dev)
     t = timed(lambda: qb.solve(Q32))
@@ -338,7 +358,7 @@ def main():
     ap.add_argument("--profile-n", type=int, default=0,
                     help="profiling target: two solves of an n-variable Gaussian FP32 instance, "
                          "no timing (for ncu)")
-    ap.add_argument("--variant", default="auto", choices=["auto", "split", "tc", "f32", "mix"],
+    ap.add_argument("--variant", default="auto", choices=["auto", "field", "split", "tc", "f32", "mix", "naive"],
                     help="kernel form of the headline solve (auto: the library's choice)")
     ap.add_argument("--alu-microbench", action="store_true",
                     help="print the ALU throughput table (roofline denominators) and exit")

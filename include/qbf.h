@@ -71,15 +71,20 @@ enum {
                               2^23 image bound does not hold (integer Q) or
                               its wider certification window overflows the
                               candidate buffer (float Q); n < 24: SPLIT     */
-    QBF_VARIANT_FIELD = 1, /* per-thread local-field vector g in registers  */
+    QBF_VARIANT_FIELD = 1, /* the plain Gray walk: per-thread field vector g
+                              in registers, n_s + 1 adds per state (suffix
+                              n_s <= 20); a reference form, not fast        */
     QBF_VARIANT_SPLIT = 2, /* field split into lane-invariant + lane parts  */
     QBF_VARIANT_TC = 3,    /* blocked form: cross term on tcgen05 tensor
                               cores, tiles of 2^14 states (15 <= n <= 42)  */
     QBF_VARIANT_SPLIT_F32 = 4, /* split walk in packed FP32 on exact integers
                                   (image < 2^23), two prefixes per thread    */
-    QBF_VARIANT_SPLIT_MIX = 5  /* split walk on both pipes: per thread three
+    QBF_VARIANT_SPLIT_MIX = 5, /* split walk on both pipes: per thread three
                                   packed-FP32 pairs and two int32 prefixes
                                   (image < 2^23, n >= 4)                     */
+    QBF_VARIANT_NAIVE = 6      /* no Gray code: every state evaluated from
+                                  scratch in natural order, O(n^2) per state;
+                                  a reference form, not fast                 */
 };
 
 typedef struct {

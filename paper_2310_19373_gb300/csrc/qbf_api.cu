@@ -175,6 +175,15 @@ int plan_geometry(int n, const qbf_options &o, Geo *g)
         if (o.prefix_bits >= 0 && o.prefix_bits != n - kTcTileSuffixBits)
             return set_err(QBF_EINVAL, "the tensor-core form fixes prefix_bits = n - 14");
         k = n - kTcTileSuffixBits;
+    } else if (o.variant == QBF_VARIANT_FIELD) {
+        // the field vector lives in registers: at most kFieldMaxSuffix suffix bits
+        if (o.prefix_bits >= 0) {
+            k = o.prefix_bits;
+            if (n - k < 1 || n - k > kFieldMaxSuffix || k > 28)
+                return set_err(QBF_EINVAL, "the field walk needs 1 <= n - prefix_bits <= 20");
+        } else {
+            k = n - std::min(auto_suffix_bits(n), kFieldMaxSuffix);
+        }
     } else if (o.variant == QBF_VARIANT_SPLIT_MIX) {
         // a lane walks nsw bits for all eight values of the group bits nsw..nsw+2
         if (n < 4)
@@ -301,13 +310,16 @@ int solve_one(const void *Q, bool host_q, int n, int dtype, const qbf_options *o
         return set_err(QBF_EINVAL, "top_k must be in [1, 64]");
     if (o.variant != QBF_VARIANT_AUTO && o.variant != QBF_VARIANT_SPLIT &&
         o.variant != QBF_VARIANT_TC && o.variant != QBF_VARIANT_SPLIT_F32 &&
-        o.variant != QBF_VARIANT_SPLIT_MIX)
+        o.variant != QBF_VARIANT_SPLIT_MIX && o.variant != QBF_VARIANT_FIELD &&
+        o.variant != QBF_VARIANT_NAIVE)
         return set_err(QBF_ENOTIMPL, "requested walk variant is not built");
     Geo g;
     if ((rc = plan_geometry(n, o, &g)))
         return rc;
     const bool tc = (o.variant == QBF_VARIANT_TC);
     const bool mix = (o.variant == QBF_VARIANT_SPLIT_MIX);
+    const bool field = (o.variant == QBF_VARIANT_FIELD);
+    const bool naive = (o.variant == QBF_VARIANT_NAIVE);
     const bool f32 = (o.variant == QBF_VARIANT_SPLIT_F32) || mix;  // same image bound
 
     const unsigned long long npref = g.p_hi - g.p_lo;
@@ -354,6 +366,10 @@ int solve_one(const void *Q, bool host_q, int n, int dtype, const qbf_options *o
     }
     if (tc)
         QBF_CUDA(launch_tc_min(plan, n, g.p_lo, g.p_hi, pmin, ctr, num_sms(), s), "tc (min)");
+    else if (field)
+        QBF_CUDA(launch_walk_field(plan, a, num_sms(), s), "walk field (min)");
+    else if (naive)
+        QBF_CUDA(launch_walk_naive(plan, a, num_sms(), s), "naive (min)");
     else if (mix)
         QBF_CUDA(launch_walk_mix(g.R, plan, recs, a, (const int *)(base + L.kbuf),
                                  (unsigned long long *)(base + L.kbuf + sizeof(int) * kKbufInts),
@@ -448,8 +464,12 @@ int solve_one(const void *Q, bool host_q, int n, int dtype, const qbf_options *o
     out->n_candidates = R->n_candidates;
     out->prefix_bits = g.k;
     out->suffix_bits = g.ns;
-    out->variant = tc ? QBF_VARIANT_TC
-                      : (mix ? QBF_VARIANT_SPLIT_MIX : (f32 ? QBF_VARIANT_SPLIT_F32 : QBF_VARIANT_SPLIT));
+    out->variant = tc      ? QBF_VARIANT_TC
+                   : mix   ? QBF_VARIANT_SPLIT_MIX
+                   : f32   ? QBF_VARIANT_SPLIT_F32
+                   : field ? QBF_VARIANT_FIELD
+                   : naive ? QBF_VARIANT_NAIVE
+                           : QBF_VARIANT_SPLIT;
     out->walk_launches = 1;
     // prepare, tables, reset, walk(min), threshold, flag, walk(emit), rescore, select
     // (+ the correction-pair conversion of the packed walk)
@@ -608,7 +628,8 @@ int qbf_prefix_minima(const void *Q_dev, int n, int dtype, int prefix_bits, int 
     if (prefix_bits < 0)
         return set_err(QBF_EINVAL, "prefix_bits must be given");
     if (variant != QBF_VARIANT_AUTO && variant != QBF_VARIANT_SPLIT && variant != QBF_VARIANT_TC &&
-        variant != QBF_VARIANT_SPLIT_F32 && variant != QBF_VARIANT_SPLIT_MIX)
+        variant != QBF_VARIANT_SPLIT_F32 && variant != QBF_VARIANT_SPLIT_MIX &&
+        variant != QBF_VARIANT_FIELD && variant != QBF_VARIANT_NAIVE)
         return set_err(QBF_ENOTIMPL, "requested walk variant is not built");
     qbf_options o;
     qbf_default_options(&o);
@@ -616,6 +637,8 @@ int qbf_prefix_minima(const void *Q_dev, int n, int dtype, int prefix_bits, int 
     o.variant = variant;
     const bool tc = (variant == QBF_VARIANT_TC);
     const bool mix = (variant == QBF_VARIANT_SPLIT_MIX);
+    const bool field = (variant == QBF_VARIANT_FIELD);
+    const bool naive = (variant == QBF_VARIANT_NAIVE);
     const bool f32 = (variant == QBF_VARIANT_SPLIT_F32) || mix;  // same image bound
     Geo g;
     int rc = plan_geometry(n, o, &g);
@@ -641,6 +664,10 @@ int qbf_prefix_minima(const void *Q_dev, int n, int dtype, int prefix_bits, int 
     const Plan *plan = (const Plan *)(base + L.plan);
     if (tc)
         QBF_CUDA(launch_tc_min(plan, n, g.p_lo, g.p_hi, pmin_dev, a.ctr, num_sms(), s), "tc (min)");
+    else if (field)
+        QBF_CUDA(launch_walk_field(plan, a, num_sms(), s), "walk field (min)");
+    else if (naive)
+        QBF_CUDA(launch_walk_naive(plan, a, num_sms(), s), "naive (min)");
     else if (mix)
         QBF_CUDA(launch_walk_mix(g.R, plan, (const Rec *)(base + L.recs), a,
                                  (const int *)(base + L.kbuf),

@@ -82,6 +82,12 @@ int release_logz();
 
 // qbf_walk_f32.cu: MIN walk in packed FP32 (image bounded by 2^23, pairs of prefixes)
 constexpr long long kF32Vmax = (1ll << 23) - (1ll << 12);
+// qbf_walk_plain.cu: the plain Gray walk (field vector, suffix <= 20 bits) and
+// the naive natural-order evaluator, on the int32 image
+constexpr int kFieldMaxSuffix = 20;
+cudaError_t launch_walk_field(const Plan *plan, const WalkArgs &a, int num_sms, cudaStream_t s);
+cudaError_t launch_walk_naive(const Plan *plan, const WalkArgs &a, int num_sms, cudaStream_t s);
+
 // qbf_ising.cu: Q = 4J + diag(2h - 2R - 2C) and c into a fixed device buffer
 // (FP64 Q for float J, h; int32 Q for integer J, h); returns Q, its dtype, c
 // and the range status on the host after synchronising s
