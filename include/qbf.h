@@ -153,6 +153,59 @@ int qbf_solve_host(const void *Q_host, int n, int dtype, const qbf_options *opt,
                    qbf_result *out, void *stream);
 
 /*
+ * Chunked, resumable enumeration (n up to QBF_MAX_N).
+ *
+ * The top `chunk_bits` variables index 2^chunk_bits chunks; each chunk is one
+ * certified qbf_solve with fix_bits = chunk_bits, fix_value = the chunk
+ * (Section 3.1's prefix split, one level up), and the chunks' top-k lists
+ * merge into the global top-k by (value, index).  A qbf_checkpoint is plain
+ * data (no pointers; 1104 bytes, fixed layout): a caller may copy it to a file
+ * after any step and resume in another process, or run shards of the chunk
+ * sequence on different GPUs or hosts and merge the finished checkpoints.
+ * The paper has no counterpart; it follows from the disjoint prefix ranges.
+ */
+#define QBF_CKPT_VERSION 1u
+typedef struct {
+    uint32_t version;       /* QBF_CKPT_VERSION                                 */
+    int32_t n, dtype;       /* the problem                                      */
+    int32_t top_k;          /* length of the merged list, 1..64                 */
+    int32_t chunk_bits;     /* chunks = values of the top chunk_bits variables  */
+    int32_t shard, nshards; /* this sequence: chunks shard, shard + nshards, ...*/
+    int32_t count;          /* valid entries of best_value / best_index         */
+    uint64_t q_hash;        /* FNV-1a of Q's bytes: steps refuse another Q      */
+    uint64_t next;          /* next position in this shard's chunk sequence     */
+    uint64_t chunks_done;   /* chunks walked (summed over merged shards)        */
+    uint64_t done_mask;     /* bit r: shard r has walked all of its chunks      */
+    uint64_t n_candidates;  /* certification candidates, summed over chunks     */
+    double error_bound;     /* largest per-chunk bound (0 for integer Q)        */
+    double best_value[QBF_MAX_TOPK];    /* ascending by (value, index)          */
+    uint64_t best_index[QBF_MAX_TOPK];
+} qbf_checkpoint;
+
+/* Start shard `shard` of `nshards` (1..64): 1 <= chunk_bits <= min(n - 1, 24),
+ * top_k 1..64.  Q_dev: device pointer, as qbf_solve (read to fingerprint it;
+ * synchronises `stream`). */
+int qbf_chunked_init(qbf_checkpoint *ck, const void *Q_dev, int n, int dtype, int top_k,
+                     int chunk_bits, int shard, int nshards, void *stream);
+
+/* Walk up to max_chunks further chunks of the shard (each a qbf_solve with
+ * `opt`, whose top_k, fix_bits and fix_value are replaced).  QBF_EINVAL if Q
+ * does not match the checkpoint's fingerprint.  When the shard's sequence
+ * ends, its bit is set in done_mask; further steps do nothing. */
+int qbf_chunked_step(qbf_checkpoint *ck, const void *Q_dev, const qbf_options *opt,
+                     uint64_t max_chunks, void *stream);
+
+/* Host only, no GPU: fold the finished shards of `other` into `into`.  Both
+ * must be finished (done_mask != 0), describe the same problem and split,
+ * and cover disjoint shards; QBF_EINVAL otherwise. */
+int qbf_chunked_merge(qbf_checkpoint *into, const qbf_checkpoint *other);
+
+/* Host only, no GPU: the result once every shard is in done_mask (min,
+ * argmin, top-k, error_bound, n_candidates; the other fields 0).  QBF_EINVAL
+ * while chunks are missing. */
+int qbf_chunked_result(const qbf_checkpoint *ck, qbf_result *out);
+
+/*
  * qbf_solve_ising -- ground state of an Ising energy by the same solver.
  *
  * The introduction (Section 1) motivates QUBO by its equivalence with the

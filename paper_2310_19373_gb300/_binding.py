@@ -64,6 +64,30 @@ class QbfResult(ctypes.Structure):
     ]
 
 
+QBF_CKPT_VERSION = 1
+
+
+class QbfCheckpoint(ctypes.Structure):
+    _fields_ = [
+        ("version", ctypes.c_uint32),
+        ("n", ctypes.c_int32),
+        ("dtype", ctypes.c_int32),
+        ("top_k", ctypes.c_int32),
+        ("chunk_bits", ctypes.c_int32),
+        ("shard", ctypes.c_int32),
+        ("nshards", ctypes.c_int32),
+        ("count", ctypes.c_int32),
+        ("q_hash", ctypes.c_uint64),
+        ("next", ctypes.c_uint64),
+        ("chunks_done", ctypes.c_uint64),
+        ("done_mask", ctypes.c_uint64),
+        ("n_candidates", ctypes.c_uint64),
+        ("error_bound", ctypes.c_double),
+        ("best_value", ctypes.c_double * QBF_MAX_TOPK),
+        ("best_index", ctypes.c_uint64 * QBF_MAX_TOPK),
+    ]
+
+
 class QbfError(RuntimeError):
     def __init__(self, status: int, msg: str):
         super().__init__(f"{STATUS_NAMES.get(status, status)}: {msg}")
@@ -79,6 +103,15 @@ _SIGS = {
                                  ctypes.POINTER(QbfResult), _VP]),
     "qbf_solve_host": (ctypes.c_int, [_VP, ctypes.c_int, ctypes.c_int,
                                       ctypes.POINTER(QbfOptions), ctypes.POINTER(QbfResult), _VP]),
+    "qbf_chunked_init": (ctypes.c_int, [ctypes.POINTER(QbfCheckpoint), _VP, ctypes.c_int,
+                                        ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int,
+                                        ctypes.c_int, _VP]),
+    "qbf_chunked_step": (ctypes.c_int, [ctypes.POINTER(QbfCheckpoint), _VP,
+                                        ctypes.POINTER(QbfOptions), ctypes.c_uint64, _VP]),
+    "qbf_chunked_merge": (ctypes.c_int, [ctypes.POINTER(QbfCheckpoint),
+                                         ctypes.POINTER(QbfCheckpoint)]),
+    "qbf_chunked_result": (ctypes.c_int, [ctypes.POINTER(QbfCheckpoint),
+                                          ctypes.POINTER(QbfResult)]),
     "qbf_solve_ising": (ctypes.c_int, [_VP, _VP, ctypes.c_int, ctypes.c_int,
                                        ctypes.POINTER(QbfOptions), ctypes.POINTER(QbfResult), _VP]),
     "qbf_solve_batched": (ctypes.c_int, [ctypes.POINTER(ctypes.c_void_p), ctypes.POINTER(ctypes.c_int),
@@ -171,6 +204,29 @@ def qbf_solve_ising(J_dev: int, h_dev: int, n: int, dtype: int, opt: QbfOptions 
                                ctypes.byref(opt) if opt is not None else None,
                                ctypes.byref(out), _VP(stream or 0))
     _check(rc)
+    return out
+
+
+def qbf_chunked_init(ck: QbfCheckpoint, Q_dev: int, n: int, dtype: int, top_k: int,
+                     chunk_bits: int, shard: int = 0, nshards: int = 1, stream: int | None = None):
+    _check(lib().qbf_chunked_init(ctypes.byref(ck), _VP(Q_dev), n, dtype, top_k, chunk_bits,
+                                  shard, nshards, _VP(stream or 0)))
+
+
+def qbf_chunked_step(ck: QbfCheckpoint, Q_dev: int, opt: QbfOptions | None, max_chunks: int,
+                     stream: int | None = None):
+    _check(lib().qbf_chunked_step(ctypes.byref(ck), _VP(Q_dev),
+                                  ctypes.byref(opt) if opt is not None else None,
+                                  max_chunks, _VP(stream or 0)))
+
+
+def qbf_chunked_merge(into: QbfCheckpoint, other: QbfCheckpoint):
+    _check(lib().qbf_chunked_merge(ctypes.byref(into), ctypes.byref(other)))
+
+
+def qbf_chunked_result(ck: QbfCheckpoint) -> QbfResult:
+    out = QbfResult()
+    _check(lib().qbf_chunked_result(ctypes.byref(ck), ctypes.byref(out)))
     return out
 
 
@@ -401,6 +457,57 @@ def solve_ising(J, h, top_k: int = 1, variant: int = QBF_VARIANT_AUTO, stream=No
     with torch.cuda.device(J.device):
         r = qbf_solve_ising(J.data_ptr(), h.data_ptr(), J.shape[0], dtype_code(J), opt, s)
     return _solution(r)
+
+
+class Chunked:
+    """Resumable enumeration of one QUBO in 2^chunk_bits chunks (shard `shard`
+    of `nshards`).  The state is a plain qbf_checkpoint: to_bytes() after any
+    step, from_bytes() to resume (in this or another process)."""
+
+    def __init__(self, ck: QbfCheckpoint):
+        self.ck = ck
+
+    @classmethod
+    def start(cls, Q, chunk_bits: int, top_k: int = 1, shard: int = 0, nshards: int = 1):
+        import torch
+
+        Q = Q.contiguous()
+        ck = QbfCheckpoint()
+        s = torch.cuda.current_stream(Q.device).cuda_stream
+        with torch.cuda.device(Q.device):
+            qbf_chunked_init(ck, Q.data_ptr(), Q.shape[0], dtype_code(Q), top_k, chunk_bits,
+                             shard, nshards, s)
+        return cls(ck)
+
+    def step(self, Q, max_chunks: int, variant: int = QBF_VARIANT_AUTO) -> bool:
+        """Walk up to max_chunks chunks; True once this shard is finished."""
+        import torch
+
+        Q = Q.contiguous()
+        s = torch.cuda.current_stream(Q.device).cuda_stream
+        with torch.cuda.device(Q.device):
+            qbf_chunked_step(self.ck, Q.data_ptr(), make_options(variant=variant), max_chunks, s)
+        return self.finished
+
+    @property
+    def finished(self) -> bool:
+        return bool(self.ck.done_mask >> self.ck.shard & 1)
+
+    def merge(self, other: "Chunked") -> "Chunked":
+        qbf_chunked_merge(self.ck, other.ck)
+        return self
+
+    def result(self) -> Solution:
+        return _solution(qbf_chunked_result(self.ck))
+
+    def to_bytes(self) -> bytes:
+        return ctypes.string_at(ctypes.addressof(self.ck), ctypes.sizeof(self.ck))
+
+    @classmethod
+    def from_bytes(cls, b: bytes) -> "Chunked":
+        if len(b) != ctypes.sizeof(QbfCheckpoint):
+            raise QbfError(QBF_EINVAL, "not a serialized qbf_checkpoint")
+        return cls(QbfCheckpoint.from_buffer_copy(b))
 
 
 def prefix_minima(Q, prefix_bits: int, variant: int = QBF_VARIANT_AUTO):

@@ -168,6 +168,10 @@ struct Geo {
 int plan_geometry(int n, const qbf_options &o, Geo *g)
 {
     int k;
+    // the automatic suffix width follows the states one call walks: with
+    // fix_bits variables fixed, n - fix_bits of them vary
+    const int fix = (o.fix_bits > 0 && o.fix_bits <= n - 1) ? o.fix_bits : 0;
+    const int nf = n - fix;
     if (o.variant == QBF_VARIANT_TC) {
         // tiles of 14 low bits are the prefixes of the certification step
         if (n < kTcTileSuffixBits + 1 || n - kTcTileSuffixBits > 28)
@@ -182,7 +186,7 @@ int plan_geometry(int n, const qbf_options &o, Geo *g)
             if (n - k < 1 || n - k > kFieldMaxSuffix || k > 28)
                 return set_err(QBF_EINVAL, "the field walk needs 1 <= n - prefix_bits <= 20");
         } else {
-            k = n - std::min(auto_suffix_bits(n), kFieldMaxSuffix);
+            k = n - std::min(auto_suffix_bits(nf), kFieldMaxSuffix);
         }
     } else if (o.variant == QBF_VARIANT_SPLIT_MIX) {
         // a lane walks nsw bits for all eight values of the group bits nsw..nsw+2
@@ -193,7 +197,7 @@ int plan_geometry(int n, const qbf_options &o, Geo *g)
             if (k > n - 4 || k > 28)
                 return set_err(QBF_EINVAL, "prefix_bits must be in [0, min(n-4, 28)] for the two-pipe walk");
         } else {
-            const int nsw = std::min(auto_suffix_bits(n), n - 3);
+            const int nsw = std::max(1, std::min(auto_suffix_bits(nf), nf - 3));
             k = n - nsw - 3;
         }
     } else if (o.variant == QBF_VARIANT_SPLIT_F32) {
@@ -205,7 +209,7 @@ int plan_geometry(int n, const qbf_options &o, Geo *g)
             if (k > n - 2 || k > 28)
                 return set_err(QBF_EINVAL, "prefix_bits must be in [0, min(n-2, 28)] for the packed walk");
         } else {
-            const int nsw = std::min(auto_suffix_bits(n), n - 1);
+            const int nsw = std::max(1, std::min(auto_suffix_bits(nf), nf - 1));
             k = n - nsw - 1;
         }
     } else if (o.prefix_bits >= 0) {
@@ -213,7 +217,7 @@ int plan_geometry(int n, const qbf_options &o, Geo *g)
         if (k > n - 1 || k > 28)
             return set_err(QBF_EINVAL, "prefix_bits must be in [0, min(n-1, 28)]");
     } else {
-        k = n - auto_suffix_bits(n);
+        k = n - auto_suffix_bits(nf);
     }
     if (o.fix_bits < 0 || o.fix_bits > n - 1)
         return set_err(QBF_EINVAL, "fix_bits must be in [0, n-1]");
@@ -504,6 +508,58 @@ int solve_locked(const void *Q, bool host_q, int n, int dtype, const qbf_options
     return solve_one(Q, host_q, n, dtype, &o, out, s);
 }
 
+// ---- chunked enumeration: host-side bookkeeping ---------------------------
+
+uint64_t fnv1a(const unsigned char *p, size_t len)
+{
+    uint64_t h = 1469598103934665603ull;
+    for (size_t i = 0; i < len; ++i) {
+        h ^= p[i];
+        h *= 1099511628211ull;
+    }
+    return h;
+}
+
+int q_fingerprint(const void *Q_dev, int n, int dtype, cudaStream_t s, uint64_t *h)
+{
+    const size_t bytes = dtype_size(dtype) * (size_t)n * n;
+    std::vector<unsigned char> buf(bytes);
+    QBF_CUDA(cudaMemcpyAsync(buf.data(), Q_dev, bytes, cudaMemcpyDeviceToHost, s), "copy Q");
+    QBF_CUDA(cudaStreamSynchronize(s), "fingerprint Q");
+    *h = fnv1a(buf.data(), bytes) ^ ((uint64_t)n << 56) ^ ((uint64_t)dtype << 48);
+    return QBF_OK;
+}
+
+// merge two ascending (value, index) lists into `val`/`idx`, keeping `cap`
+int merge_lists(const double *va, const uint64_t *ia, int na, const double *vb,
+                const uint64_t *ib, int nb, int cap, double *val, uint64_t *idx)
+{
+    double tv[2 * QBF_MAX_TOPK];
+    uint64_t ti[2 * QBF_MAX_TOPK];
+    int a = 0, b = 0, c = 0;
+    while (c < cap && (a < na || b < nb)) {
+        const bool take_a =
+            b >= nb || (a < na && (va[a] < vb[b] || (va[a] == vb[b] && ia[a] < ib[b])));
+        if (take_a) {
+            tv[c] = va[a];
+            ti[c++] = ia[a++];
+        } else {
+            tv[c] = vb[b];
+            ti[c++] = ib[b++];
+        }
+    }
+    for (int i = 0; i < c; ++i) {
+        val[i] = tv[i];
+        idx[i] = ti[i];
+    }
+    return c;
+}
+
+uint64_t all_shards(int nshards)
+{
+    return nshards >= 64 ? ~0ull : ((1ull << nshards) - 1);
+}
+
 }  // namespace
 
 namespace qbf {
@@ -561,6 +617,125 @@ int qbf_solve_ising(const void *J_dev, const void *h_dev, int n, int dtype,
     out->min_value += c;
     for (int i = 0; i < out->top_k; ++i)
         out->topk_value[i] += c;
+    return QBF_OK;
+}
+
+int qbf_chunked_init(qbf_checkpoint *ck, const void *Q_dev, int n, int dtype, int top_k,
+                     int chunk_bits, int shard, int nshards, void *stream)
+{
+    std::lock_guard<std::mutex> lk(g_mu);
+    if (!ck || !Q_dev)
+        return set_err(QBF_EINVAL, "null pointer argument");
+    if (n < 2 || n > QBF_MAX_N)
+        return set_err(QBF_EINVAL, "n must be in [2, 48]");
+    if (dtype_size(dtype) == 0)
+        return set_err(QBF_EDTYPE, "unknown dtype");
+    if (top_k < 1 || top_k > QBF_MAX_TOPK)
+        return set_err(QBF_EINVAL, "top_k must be in [1, 64]");
+    if (chunk_bits < 1 || chunk_bits > std::min(n - 1, 24))
+        return set_err(QBF_EINVAL, "chunk_bits must be in [1, min(n-1, 24)]");
+    if (nshards < 1 || nshards > 64 || shard < 0 || shard >= nshards)
+        return set_err(QBF_EINVAL, "need 0 <= shard < nshards <= 64");
+    memset(ck, 0, sizeof(*ck));
+    ck->version = QBF_CKPT_VERSION;
+    ck->n = n;
+    ck->dtype = dtype;
+    ck->top_k = top_k;
+    ck->chunk_bits = chunk_bits;
+    ck->shard = shard;
+    ck->nshards = nshards;
+    if ((uint64_t)shard >= (1ull << chunk_bits))
+        ck->done_mask = 1ull << shard;  // no chunk falls to this shard
+    return q_fingerprint(Q_dev, n, dtype, (cudaStream_t)stream, &ck->q_hash);
+}
+
+int qbf_chunked_step(qbf_checkpoint *ck, const void *Q_dev, const qbf_options *opt,
+                     uint64_t max_chunks, void *stream)
+{
+    std::lock_guard<std::mutex> lk(g_mu);
+    cudaStream_t s = (cudaStream_t)stream;
+    if (!ck || !Q_dev)
+        return set_err(QBF_EINVAL, "null pointer argument");
+    if (ck->version != QBF_CKPT_VERSION || ck->nshards < 1 || ck->nshards > 64)
+        return set_err(QBF_EINVAL, "not a checkpoint of this library version");
+    uint64_t h = 0;
+    int rc = q_fingerprint(Q_dev, ck->n, ck->dtype, s, &h);
+    if (rc)
+        return rc;
+    if (h != ck->q_hash)
+        return set_err(QBF_EINVAL, "the checkpoint belongs to another Q");
+    const uint64_t nchunks = 1ull << ck->chunk_bits;
+    qbf_options o;
+    qbf_default_options(&o);
+    if (opt)
+        o = *opt;
+    o.top_k = ck->top_k;
+    o.fix_bits = ck->chunk_bits;
+    for (uint64_t done = 0; done < max_chunks; ++done) {
+        const uint64_t chunk = (uint64_t)ck->shard + ck->next * (uint64_t)ck->nshards;
+        if (chunk >= nchunks) {
+            ck->done_mask |= 1ull << ck->shard;
+            break;
+        }
+        o.fix_value = chunk;
+        qbf_result r;
+        if ((rc = solve_locked(Q_dev, false, ck->n, ck->dtype, &o, &r, s)))
+            return rc;
+        ck->count = merge_lists(ck->best_value, ck->best_index, ck->count, r.topk_value,
+                                r.topk_index, r.top_k, ck->top_k, ck->best_value, ck->best_index);
+        ck->error_bound = std::max(ck->error_bound, r.error_bound);
+        ck->n_candidates += r.n_candidates;
+        ck->chunks_done += 1;
+        ck->next += 1;
+        if ((uint64_t)ck->shard + ck->next * (uint64_t)ck->nshards >= nchunks)
+            ck->done_mask |= 1ull << ck->shard;
+    }
+    return QBF_OK;
+}
+
+int qbf_chunked_merge(qbf_checkpoint *into, const qbf_checkpoint *other)
+{
+    if (!into || !other)
+        return set_err(QBF_EINVAL, "null pointer argument");
+    if (into->version != QBF_CKPT_VERSION || other->version != QBF_CKPT_VERSION)
+        return set_err(QBF_EINVAL, "not a checkpoint of this library version");
+    if (into->n != other->n || into->dtype != other->dtype || into->top_k != other->top_k ||
+        into->chunk_bits != other->chunk_bits || into->nshards != other->nshards ||
+        into->q_hash != other->q_hash)
+        return set_err(QBF_EINVAL, "checkpoints of different problems or splits");
+    if (!into->done_mask || !other->done_mask)
+        return set_err(QBF_EINVAL, "only finished shards merge");
+    if (into->done_mask & other->done_mask)
+        return set_err(QBF_EINVAL, "the checkpoints share a shard");
+    into->count = merge_lists(into->best_value, into->best_index, into->count, other->best_value,
+                              other->best_index, other->count, into->top_k, into->best_value,
+                              into->best_index);
+    into->chunks_done += other->chunks_done;
+    into->n_candidates += other->n_candidates;
+    into->error_bound = std::max(into->error_bound, other->error_bound);
+    into->done_mask |= other->done_mask;
+    return QBF_OK;
+}
+
+int qbf_chunked_result(const qbf_checkpoint *ck, qbf_result *out)
+{
+    if (!ck || !out)
+        return set_err(QBF_EINVAL, "null pointer argument");
+    if (ck->version != QBF_CKPT_VERSION || ck->nshards < 1 || ck->nshards > 64)
+        return set_err(QBF_EINVAL, "not a checkpoint of this library version");
+    if (ck->done_mask != all_shards(ck->nshards) || ck->chunks_done != (1ull << ck->chunk_bits) ||
+        ck->count < 1)
+        return set_err(QBF_EINVAL, "chunks are still missing");
+    memset(out, 0, sizeof(*out));
+    out->top_k = ck->count;
+    for (int i = 0; i < ck->count; ++i) {
+        out->topk_value[i] = ck->best_value[i];
+        out->topk_index[i] = ck->best_index[i];
+    }
+    out->min_value = ck->best_value[0];
+    out->argmin = ck->best_index[0];
+    out->error_bound = ck->error_bound;
+    out->n_candidates = ck->n_candidates;
     return QBF_OK;
 }
 
