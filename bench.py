@@ -207,6 +207,29 @@ def run_profile_case(n, variant=0):
                       "walk_ms": sol.walk_seconds * 1e3}))
 
 
+def run_profile_batched(count, variant=0):
+    """Two batched solves on the first `count` instances of the 4096-instance
+    workload (a small case for ncu)."""
+    import numpy as np
+    import torch
+
+    import __graft_entry__
+
+    __graft_entry__.build()
+    from paper_2310_19373_gb300 import _binding as qb
+    from paper_2310_19373_gb300 import inputs
+
+    Qs = [torch.from_numpy(np.ascontiguousarray(q)).cuda()
+          for q in inputs.config_batched(count=count)]
+    for _ in range(2):
+        t0 = time.perf_counter()
+        vmin, am = qb.solve_batched(Qs, variant=variant)
+        torch.cuda.synchronize()
+        dt = time.perf_counter() - t0
+    states = float(sum(2 ** q.shape[0] for q in Qs))
+    print(json.dumps({"profile_batched": count, "seconds": dt, "states_per_s": states / dt}))
+
+
 ALU_OPS = ["IADD3", "IMNMX", "3-input integer min", "FADD", "FFMA", "FMNMX", "3-input FMNMX",
            "packed FADD (f32x2)", "IADD3 + IMNMX pair", "FADD + FMNMX pair"]
 
@@ -374,6 +397,8 @@ def main():
                          "no timing (for ncu)")
     ap.add_argument("--variant", default="auto", choices=["auto", "field", "split", "tc", "f32", "mix", "naive"],
                     help="kernel form of the headline solve (auto: the library's choice)")
+    ap.add_argument("--profile-batched", type=int, default=0,
+                    help="run two batched solves on this many instances of the batched workload")
     ap.add_argument("--alu-microbench", action="store_true",
                     help="print the ALU throughput table (roofline denominators) and exit")
     args = ap.parse_args()
@@ -391,6 +416,9 @@ def main():
         return
     if args.alu_microbench:
         run_alu_microbench()
+        return
+    if args.profile_batched:
+        run_profile_batched(args.profile_batched, VARIANTS[args.variant])
         return
 
     import numpy as np

@@ -260,13 +260,14 @@ def qbf_tune_batched(Q_ptrs, ns, dtypes, lo_bits: int = 6, hi_bits: int = 16,
     return best.value, sec.value
 
 
-def solve_batched(Qs, batch_suffix_bits: int = 0, stream=None):
+def solve_batched(Qs, batch_suffix_bits: int = 0, stream=None, variant: int = QBF_VARIANT_AUTO):
     """Minimise a list of square CUDA tensors; returns (min_values, argmins)."""
     import torch
 
     Qs = [q.contiguous() for q in Qs]
     opt = qbf_default_options()
     opt.batch_suffix_bits = batch_suffix_bits
+    opt.variant = variant
     s = stream if stream is not None else torch.cuda.current_stream().cuda_stream
     return qbf_solve_batched([q.data_ptr() for q in Qs], [q.shape[0] for q in Qs],
                              [dtype_code(q) for q in Qs], opt, s)

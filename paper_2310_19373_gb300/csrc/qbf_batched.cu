@@ -33,6 +33,7 @@
 #include "qbf_internal.cuh"
 #include "qbf_kernels.cuh"
 #include "qbf_walk_core.cuh"
+#include "qbf_walk_mix_core.cuh"
 
 namespace qbf {
 
@@ -43,8 +44,12 @@ constexpr int kBatchWarps = kBatchThreads / 32;
 constexpr int kBatchR = kRMax;
 constexpr int kBatchMaxNS = 16;
 constexpr int kBatchMinN = 11;  // smallest walk dimension: ns >= R and 32 prefixes per item
+// per warp: the 16-byte correction records of the two-pipe walk (128 x int4,
+// first so they stay 16-byte aligned), then S, lin, K and the lane parts of
+// the fields
 constexpr int kWarpSmemInts =
-    QBF_BATCH_MAX_N * QBF_BATCH_MAX_N + QBF_BATCH_MAX_N + 128 + 2 * (kBatchMaxNS - kBatchR) * 32;
+    (512 + QBF_BATCH_MAX_N * QBF_BATCH_MAX_N + QBF_BATCH_MAX_N + 128 +
+     2 * (kBatchMaxNS - kBatchR) * 32 + 3) & ~3;
 constexpr unsigned long long kBatchCandCap = 1ull << 20;
 
 struct BatchArgs {
@@ -61,7 +66,10 @@ struct BatchArgs {
     unsigned long long *cand_idx;
     unsigned *cand_inst;
     unsigned long long cap;
+    int mix;  // MIN walk: the two-pipe form for instances whose image fits 2^23
 };
+
+
 
 __device__ __forceinline__ void emit_candidate(const BatchArgs &a, unsigned long long idx, int inst)
 {
@@ -88,11 +96,12 @@ __device__ __forceinline__ int find_instance(const BatchDesc *d, int count, unsi
 template <int MODE>
 __global__ void __launch_bounds__(kBatchThreads) batched_walk_kernel(BatchArgs a)
 {
-    __shared__ int sm[kBatchWarps][kWarpSmemInts];
+    __shared__ __align__(16) int sm[kBatchWarps][kWarpSmemInts];
     const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    int *sS = sm[w];
+    int4 *sKx = reinterpret_cast<int4 *>(sm[w]);
+    int *sS = sm[w] + 512;
     int *sLin = sS, *sK = sS, *sC = sS;
-    int cur = -1, n = 0, ns = 0, tau = 0, ok = 0, exact = 0;
+    int cur = -1, n = 0, ns = 0, tau = 0, ok = 0, exact = 0, use_mix = 0;
     unsigned long long nprefix = 0, item_off = 0;
     const int4 *rec4 = nullptr;
     const unsigned long long total =
@@ -124,8 +133,16 @@ __global__ void __launch_bounds__(kBatchThreads) batched_walk_kernel(BatchArgs a
                 sS[e] = plan->S[e];
             for (int e = lane; e < n; e += 32)
                 sLin[e] = plan->lin[e];
-            for (int e = lane; e < 128; e += 32)
-                sK[e] = a.K[inst * 128 + e];
+            for (int e = lane; e < 128; e += 32) {
+                const int k = a.K[inst * 128 + e];
+                const int kf = __float_as_int((float)k);  // exact when the image fits 2^23
+                sK[e] = k;
+                sKx[e] = make_int4(kf, kf, k, 0);
+            }
+            // two-pipe walk: every partial sum must be exact in FP32, and the
+            // lane needs R walked bits below its three group bits
+            use_mix = (MODE == kModeMin) && a.mix && ok && ns >= kBatchR + 3 &&
+                      plan->vhat <= (long long)kF32Vmax;
             if (MODE == kModeEmit && ok) {
                 const long long t = (long long)a.gmin[inst] + plan->window;
                 tau = (int)(t > (long long)INT_MAX ? (long long)INT_MAX : t);
@@ -139,10 +156,17 @@ __global__ void __launch_bounds__(kBatchThreads) batched_walk_kernel(BatchArgs a
         const unsigned long long pl = (gi - item_off) * 32 + lane;
         const bool active = pl < nprefix;
         const unsigned long long p = active ? pl : 0;
-        unsigned GL[kBatchR];
-        const unsigned v = lane_setup<kBatchR>(p, n, ns, sS, sLin, sC, 32, lane, GL);
         if constexpr (MODE == kModeMin) {
-            const int m = walk_suffix_min<kBatchR>(v, GL, ns, rec4, sC, 32, lane, SmemK{sK});
+            int m;
+            if (use_mix) {
+                mix::Lane<kBatchR> L;
+                mix::setup<kBatchR>(L, p, n, ns, sS, sLin, sC, 32, lane);
+                m = mix::walk_min_rt<kBatchR>(L, n, ns, rec4, sC, sS, 32, lane, sKx);
+            } else {
+                unsigned GL[kBatchR];
+                const unsigned v = lane_setup<kBatchR>(p, n, ns, sS, sLin, sC, 32, lane, GL);
+                m = walk_suffix_min<kBatchR>(v, GL, ns, rec4, sC, 32, lane, SmemK{sK});
+            }
             int wm = active ? m : INT_MAX;
 #pragma unroll
             for (int o = 16; o > 0; o >>= 1)
@@ -154,6 +178,8 @@ __global__ void __launch_bounds__(kBatchThreads) batched_walk_kernel(BatchArgs a
         } else if (exact) {
             // W = 0: the values are exact, so only the lowest tied index of
             // each lane can win; emit that one state per lane
+            unsigned GL[kBatchR];
+            const unsigned v = lane_setup<kBatchR>(p, n, ns, sS, sLin, sC, 32, lane, GL);
             const unsigned long long pbase = p << ns;
             unsigned long long best = ~0ull;
             walk_suffix_visit<kBatchR>(v, GL, ns, rec4, sC, 32, lane, SmemK{sK},
@@ -167,6 +193,8 @@ __global__ void __launch_bounds__(kBatchThreads) batched_walk_kernel(BatchArgs a
             if (active && best != ~0ull)
                 emit_candidate(a, best, inst);
         } else {
+            unsigned GL[kBatchR];
+            const unsigned v = lane_setup<kBatchR>(p, n, ns, sS, sLin, sC, 32, lane, GL);
             const unsigned long long pbase = p << ns;
             walk_suffix_visit<kBatchR>(v, GL, ns, rec4, sC, 32, lane, SmemK{sK},
                                        [&](unsigned val, unsigned t) {
@@ -383,6 +411,7 @@ BStage bstage(int count)
 struct GraphKey {
     int count;
     int ns_max;
+    int mix;
     unsigned long long nrec, items;
     void *dev, *host;
     int grid_min, grid_emit;
@@ -425,7 +454,7 @@ int walk_bps(int mode)
     } while (0)
 
 int enqueue_batch(BatchState &B, const BLayout &L, const BStage &S, int count,
-                  unsigned long long items, int grid_min, int grid_emit, cudaStream_t s)
+                  unsigned long long items, int grid_min, int grid_emit, int mix, cudaStream_t s)
 {
     char *d = (char *)B.dev;
     char *h = (char *)B.host;
@@ -444,7 +473,8 @@ int enqueue_batch(BatchState &B, const BLayout &L, const BStage &S, int count,
     unsigned *lowest = (unsigned *)(d + L.lowest);
     batched_reset_kernel<<<(count + 255) / 256, 256, 0, s>>>(count, gmin, best_key, best_idx,
                                                              lowest, ctr);
-    batched_prepare_kernel<<<count, 256, 0, s>>>(desc, plans, (int *)(d + L.status));
+    batched_prepare_kernel<<<count, 256, 0, s>>>(desc, plans, (int *)(d + L.status),
+                                                 mix ? kF32Vmax : (long long)INT_MAX);
     batched_tables_kernel<<<count, 256, 0, s>>>(desc, plans, recs, K);
     BatchArgs a;
     memset(&a, 0, sizeof(a));
@@ -461,6 +491,7 @@ int enqueue_batch(BatchState &B, const BLayout &L, const BStage &S, int count,
     a.cand_idx = (unsigned long long *)(d + L.cand_idx);
     a.cand_inst = (unsigned *)(d + L.cand_inst);
     a.cap = kBatchCandCap;
+    a.mix = mix;
     batched_walk_kernel<kModeMin><<<grid_min, kBatchThreads, 0, s>>>(a);
     const int fb = (int)std::min<unsigned long long>((items + 255) / 256, 8192);
     batched_flag_kernel<<<fb, 256, 0, s>>>(desc, count, plans, a.item_min, gmin, items,
@@ -495,9 +526,11 @@ int dtsize(int dt)
 
 }  // namespace
 
-int solve_batched(const void *const *Q, const int *n, const int *dtype, int count,
-                  const qbf_options *opt_in, double *min_value, uint64_t *argmin,
-                  cudaStream_t s, int *kernel_launches)
+// One batched pass; mix = 1: float instances take the 2^23 image and every
+// instance whose image fits it takes the two-pipe MIN walk.
+int solve_batched_mode(const void *const *Q, const int *n, const int *dtype, int count,
+                       const qbf_options *opt_in, double *min_value, uint64_t *argmin,
+                       cudaStream_t s, int *kernel_launches, int mix)
 {
     if (!Q || !n || !dtype || !min_value || !argmin)
         return record_error(QBF_EINVAL, "null pointer argument");
@@ -588,6 +621,7 @@ int solve_batched(const void *const *Q, const int *n, const int *dtype, int coun
     memset(&key, 0, sizeof(key));
     key.count = count;
     key.ns_max = ns_max;
+    key.mix = mix;
     key.nrec = nrec;
     key.items = items;
     key.dev = B.dev;
@@ -602,7 +636,7 @@ int solve_batched(const void *const *Q, const int *n, const int *dtype, int coun
         cudaGraph_t graph = nullptr;
         B_CUDA(cudaStreamBeginCapture(B.cap_stream, cudaStreamCaptureModeThreadLocal),
                "begin capture");
-        int rc = enqueue_batch(B, L, S, count, items, grid_min, grid_emit, B.cap_stream);
+        int rc = enqueue_batch(B, L, S, count, items, grid_min, grid_emit, mix, B.cap_stream);
         cudaError_t ce = cudaStreamEndCapture(B.cap_stream, &graph);
         if (rc)
             return rc;
@@ -647,6 +681,28 @@ int solve_batched(const void *const *Q, const int *n, const int *dtype, int coun
         argmin[i] = bi[i];
     }
     return QBF_OK;
+}
+
+// QBF_VARIANT_AUTO / SPLIT_MIX: the two-pipe pass; AUTO repeats the batch on
+// the int32 walk (2^31 images) if the wider windows of the FP32 images flag
+// more candidates than the buffer holds.  QBF_VARIANT_SPLIT: the int32 pass.
+int solve_batched(const void *const *Q, const int *n, const int *dtype, int count,
+                  const qbf_options *opt_in, double *min_value, uint64_t *argmin,
+                  cudaStream_t s, int *kernel_launches)
+{
+    const int variant = opt_in ? opt_in->variant : QBF_VARIANT_AUTO;
+    if (variant != QBF_VARIANT_AUTO && variant != QBF_VARIANT_SPLIT &&
+        variant != QBF_VARIANT_SPLIT_MIX)
+        return record_error(QBF_ENOTIMPL, "qbf_solve_batched runs the int32 or two-pipe walk");
+    if (variant == QBF_VARIANT_SPLIT)
+        return solve_batched_mode(Q, n, dtype, count, opt_in, min_value, argmin, s,
+                                  kernel_launches, 0);
+    const int rc = solve_batched_mode(Q, n, dtype, count, opt_in, min_value, argmin, s,
+                                      kernel_launches, 1);
+    if (rc == QBF_EOVERFLOW && variant == QBF_VARIANT_AUTO)
+        return solve_batched_mode(Q, n, dtype, count, opt_in, min_value, argmin, s,
+                                  kernel_launches, 0);
+    return rc;
 }
 
 int set_tuned_batch_ns(int ns)

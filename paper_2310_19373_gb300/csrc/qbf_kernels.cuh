@@ -34,7 +34,8 @@ struct WalkArgs {
 
 // qbf_prepare.cu
 __global__ void prepare_kernel(const void *Q, int n, int dtype, Plan *plan, long long vmax);
-__global__ void batched_prepare_kernel(const BatchDesc *desc, Plan *plans, int *status);
+__global__ void batched_prepare_kernel(const BatchDesc *desc, Plan *plans, int *status,
+                                       long long vmax_float);
 __global__ void batched_tables_kernel(const BatchDesc *desc, const Plan *plans, Rec *recs, int *K);
 __global__ void logz_prepare_kernel(const void *Q, int n, int dtype, int rot, Plan *plans);
 __global__ void logz_tables_kernel(const Plan *plans, int nsA, int nsB, Rec *recs,

@@ -272,11 +272,14 @@ __global__ void tables_kernel(const Plan *__restrict__ plan, int ns, int R, Rec 
 // ---- batched: one CTA per instance ---------------------------------------
 
 __global__ void __launch_bounds__(256) batched_prepare_kernel(const BatchDesc *desc, Plan *plans,
-                                                              int *status)
+                                                              int *status, long long vmax_float)
 {
     const BatchDesc d = desc[blockIdx.x];
     Plan *plan = plans + blockIdx.x;
-    prepare_body(d.Q, d.n_src, d.n, d.dtype, plan, (long long)INT_MAX);
+    // integer instances keep their exact image (2^31 bound); float instances
+    // are scaled into vmax_float
+    const bool is_int = (d.dtype == QBF_I32 || d.dtype == QBF_I16);
+    prepare_body(d.Q, d.n_src, d.n, d.dtype, plan, is_int ? (long long)INT_MAX : vmax_float);
     if (threadIdx.x == 0)
         status[blockIdx.x] = plan->status;
 }

@@ -22,88 +22,22 @@
 // unchanged.
 #include <climits>
 
-#include "qbf_f32x2.cuh"
 #include "qbf_internal.cuh"
 #include "qbf_kernels.cuh"
-#include "qbf_walk_core.cuh"
+#include "qbf_walk_mix_core.cuh"
 
 namespace qbf {
 
-__constant__ int c_Km[2][64];                  // K[parity][u] (int32 streams)
-__constant__ unsigned long long c_K2m[2][64];  // (K, K) as FP32 pairs (packed streams)
+__constant__ int c_Km[2][64];                  // K[parity][u] (int32 groups)
+__constant__ unsigned long long c_K2m[2][64];  // (K, K) as FP32 pairs (packed groups)
 
 namespace {
 
-using f32x2::u64;
-
-// one block of 2^R - 1 in-block steps of parity PI
-template <int R, int PI>
-__device__ __forceinline__ void mix_block(u64 (&vF)[3], float (&mF)[3], unsigned (&vI)[2], int &mI,
-                                          const u64 (&GF)[3][R], const unsigned (&GI)[2][R])
-{
-#pragma unroll
-    for (int u = 1; u < (1 << R); ++u) {
-        const int l = ctz_c(u);
-        const int g = u ^ (u >> 1);
-        const int nb = ((g >> l) & 1) ^ ((l == R - 1) ? PI : 0);
-#pragma unroll
-        for (int s = 0; s < 3; ++s) {
-            u64 v = nb ? f32x2::add(vF[s], GF[s][l]) : f32x2::sub(vF[s], GF[s][l]);
-            v = f32x2::add(v, c_K2m[PI][u]);
-            float lo, hi;
-            f32x2::unpack(v, lo, hi);
-            mF[s] = f32x2::min3(mF[s], lo, hi);
-            vF[s] = v;
-        }
-        const unsigned k = (unsigned)c_Km[PI][u];
-        vI[0] = vI[0] + (nb ? GI[0][l] : 0u - GI[0][l]) + k;
-        vI[1] = vI[1] + (nb ? GI[1][l] : 0u - GI[1][l]) + k;
-        mI = __vimin3_s32(mI, (int)vI[0], (int)vI[1]);
-    }
-}
-
-// Block transition: record (ra, rb) = (T, code, W0..W5).  The flipped mid bit
-// is i = R + (code >> 1), entered with sign + if code is odd; its field for
-// group b is T (signed, lane-invariant) + sign * (c_i + b0 s0 + b1 s1 + b2 s2)
-// with c_i the lane part from the prefix and s_t = S[i][nsw + t].
-template <int R>
-__device__ __forceinline__ void mix_trans(u64 (&vF)[3], float (&mF)[3], unsigned (&vI)[2], int &mI,
-                                          u64 (&GF)[3][R], unsigned (&GI)[2][R], const int4 ra,
-                                          const int4 rb, const int *sC, const int *sS, int n,
-                                          int nsw, int stride, int slot)
-{
-    const int rel = ra.y >> 1;
-    const bool plus = ra.y & 1;
-    const int *Si = sS + (R + rel) * n + nsw;
-    const int c = sC[rel * stride + slot];
-    const int cs = plus ? c : -c;
-    const int t0 = plus ? Si[0] : -Si[0];
-    const int t1 = plus ? Si[1] : -Si[1];
-    const int t2 = plus ? Si[2] : -Si[2];
-    const int base = ra.x + cs;
-    vF[0] = f32x2::add(vF[0], f32x2::pack((float)base, (float)(base + t0)));
-    vF[1] = f32x2::add(vF[1], f32x2::pack((float)(base + t1), (float)(base + t1 + t0)));
-    vF[2] = f32x2::add(vF[2], f32x2::pack((float)(base + t2), (float)(base + t2 + t0)));
-    vI[0] += (unsigned)(base + t1 + t2);
-    vI[1] += (unsigned)(base + t0 + t1 + t2);
-#pragma unroll
-    for (int s = 0; s < 3; ++s) {
-        float lo, hi;
-        f32x2::unpack(vF[s], lo, hi);
-        mF[s] = f32x2::min3(mF[s], lo, hi);
-    }
-    mI = __vimin3_s32(mI, (int)vI[0], (int)vI[1]);
-    const int W[6] = {ra.z, ra.w, rb.x, rb.y, rb.z, rb.w};
-#pragma unroll
-    for (int i = 0; i < R; ++i) {
-        const u64 w2 = f32x2::splat((float)W[i]);
-#pragma unroll
-        for (int s = 0; s < 3; ++s)
-            GF[s][i] = f32x2::add(GF[s][i], w2);
-        GI[0][i] += (unsigned)W[i];
-        GI[1][i] += (unsigned)W[i];
-    }
-}
+// corrections from the constant bank (one instance per launch)
+struct ConstKm {
+    __device__ __forceinline__ int k(int pi, int u) const { return c_Km[pi][u]; }
+    __device__ __forceinline__ unsigned long long k2(int pi, int u) const { return c_K2m[pi][u]; }
+};
 
 }  // namespace
 
@@ -116,9 +50,7 @@ __global__ void __launch_bounds__(kWalkThreads) walk_mix_min_kernel(const Plan *
 {
     extern __shared__ int smem[];
     const int n = a.n;
-    const int nsg = a.ns;     // suffix bits incl. the group bits
-    const int nsw = nsg - 3;  // walked bits
-    const int kp = n - nsg;   // prefix bits of a lane
+    const int nsg = a.ns;  // suffix bits incl. the group bits
     int *sS = smem;
     int *sLin = sS + n * n;
     int *sC = sLin + n;  // lane parts of the mid-bit fields, (nsw - R) x blockDim
@@ -131,8 +63,6 @@ __global__ void __launch_bounds__(kWalkThreads) walk_mix_min_kernel(const Plan *
         return;
     const int lane = threadIdx.x & 31;
     const int4 *rec4 = reinterpret_cast<const int4 *>(recs);
-    const int M = nsw - R;
-    const unsigned nblocks = 1u << M;
     const int stride = blockDim.x, slot = threadIdx.x;
 
     while (true) {
@@ -145,81 +75,9 @@ __global__ void __launch_bounds__(kWalkThreads) walk_mix_min_kernel(const Plan *
         const unsigned long long i = a.p_lo + item * 32 + lane;
         const bool active = i < a.p_hi;
         const unsigned long long p = active ? i : a.p_lo;
-
-        // value of (prefix, group 0, suffix 0) and the group bits' fields
-        int va = 0;
-        for (int j = 0; j < kp; ++j) {
-            if (!((p >> j) & 1))
-                continue;
-            const int vj = nsg + j;
-            int row = sLin[vj];
-            for (int jj = j + 1; jj < kp; ++jj)
-                if ((p >> jj) & 1)
-                    row += sS[vj * n + nsg + jj];
-            va += row;
-        }
-        int gf[3];
-#pragma unroll
-        for (int t = 0; t < 3; ++t) {
-            int f = sLin[nsw + t];
-            for (int j = 0; j < kp; ++j)
-                if ((p >> j) & 1)
-                    f += sS[(nsw + t) * n + nsg + j];
-            gf[t] = f;
-        }
-        const int s01 = sS[nsw * n + nsw + 1], s02 = sS[nsw * n + nsw + 2];
-        const int s12 = sS[(nsw + 1) * n + nsw + 2];
-        // v(b) = va + sum_t b_t gf_t + sum_{t<t'} b_t b_t' S_tt'
-        const int v000 = va, v001 = va + gf[0];
-        const int v010 = va + gf[1], v011 = v010 + gf[0] + s01;
-        const int v100 = va + gf[2], v101 = v100 + gf[0] + s02;
-        const int v110 = v010 + gf[2] + s12, v111 = v011 + gf[2] + s02 + s12;
-        u64 vF[3] = {f32x2::pack((float)v000, (float)v001), f32x2::pack((float)v010, (float)v011),
-                     f32x2::pack((float)v100, (float)v101)};
-        unsigned vI[2] = {(unsigned)v110, (unsigned)v111};
-        u64 GF[3][R];
-        unsigned GI[2][R];
-#pragma unroll
-        for (int ii = 0; ii < R; ++ii) {
-            int c = sLin[ii];
-            for (int j = 0; j < kp; ++j)
-                if ((p >> j) & 1)
-                    c += sS[ii * n + nsg + j];
-            const int s0 = sS[ii * n + nsw], s1 = sS[ii * n + nsw + 1], s2 = sS[ii * n + nsw + 2];
-            GF[0][ii] = f32x2::pack((float)c, (float)(c + s0));
-            GF[1][ii] = f32x2::pack((float)(c + s1), (float)(c + s1 + s0));
-            GF[2][ii] = f32x2::pack((float)(c + s2), (float)(c + s2 + s0));
-            GI[0][ii] = (unsigned)(c + s1 + s2);
-            GI[1][ii] = (unsigned)(c + s0 + s1 + s2);
-        }
-        for (int ii = R; ii < nsw; ++ii) {
-            int c = 0;
-            for (int j = 0; j < kp; ++j)
-                if ((p >> j) & 1)
-                    c += sS[ii * n + nsg + j];
-            sC[(ii - R) * stride + slot] = c;
-        }
-        float mF[3] = {fminf((float)v000, (float)v001), fminf((float)v010, (float)v011),
-                       fminf((float)v100, (float)v101)};
-        int mI = min(v110, v111);
-        if (M == 0) {
-            mix_block<R, 0>(vF, mF, vI, mI, GF, GI);
-        } else {
-            for (unsigned B = 0; B < nblocks; B += 2) {
-                const int4 r1a = __ldg(rec4 + 2 * (B + 1));
-                const int4 r1b = __ldg(rec4 + 2 * (B + 1) + 1);
-                const unsigned B2 = (B + 2 < nblocks) ? B + 2 : B + 1;
-                const int4 r2a = __ldg(rec4 + 2 * B2);
-                const int4 r2b = __ldg(rec4 + 2 * B2 + 1);
-                mix_block<R, 0>(vF, mF, vI, mI, GF, GI);
-                mix_trans<R>(vF, mF, vI, mI, GF, GI, r1a, r1b, sC, sS, n, nsw, stride, slot);
-                mix_block<R, 1>(vF, mF, vI, mI, GF, GI);
-                if (B + 2 < nblocks)
-                    mix_trans<R>(vF, mF, vI, mI, GF, GI, r2a, r2b, sC, sS, n, nsw, stride, slot);
-            }
-        }
-        // exact: integers below 2^23
-        const int mi = min(min((int)mF[0], (int)mF[1]), min((int)mF[2], mI));
+        mix::Lane<R> L;
+        mix::setup<R>(L, p, n, nsg, sS, sLin, sC, stride, slot);
+        const int mi = mix::walk_min<R>(L, n, nsg, rec4, sC, sS, stride, slot, ConstKm{});
         if (active)
             a.pmin[p - a.p_lo] = mi;
         int wm = active ? mi : INT_MAX;

@@ -103,3 +103,51 @@ def test_batched_tuner_and_repeat():
     for i, Q in enumerate(Qs):
         v, a = oracle.brute_min(Q)
         assert (first[0][i], first[1][i]) == (float(v), a)
+
+
+def test_batched_two_pipe_matches_int32_pass():
+    """AUTO (the two-pipe MIN walk for instances whose image fits 2^23) and
+    QBF_VARIANT_SPLIT (the int32 walk throughout) certify the same answers on
+    a mixed batch: FP32/FP64 and integer instances, small n (int32 walk inside
+    the two-pipe pass) and large n, and an integer instance too large for the
+    2^23 image."""
+    rng = np.random.default_rng(77)
+    Qs = []
+    for i, n in enumerate([12, 16, 19, 22, 24, 26, 27, 25, 23, 20]):
+        if i % 3 == 0:
+            Qs.append(rng.integers(-50, 51, size=(n, n)).astype(np.int16))
+        elif i % 3 == 1:
+            Qs.append(rng.normal(size=(n, n)).astype(np.float32))
+        else:
+            Qs.append(np.triu(rng.uniform(-1, 1, size=(n, n))))
+    big = np.triu(rng.integers(-100000, 100001, size=(24, 24))).astype(np.int32)
+    assert np.abs(big.astype(np.int64)).sum() >= 2 ** 23
+    Qs.append(big)
+    dQs = to_dev(Qs)
+    a = qb.solve_batched(dQs)
+    b = qb.solve_batched(dQs, variant=qb.QBF_VARIANT_SPLIT)
+    assert a == b
+    for Q, v, x in zip(Qs, *a):
+        ov, ox = oracle.brute_min(Q)
+        assert (v, x) == (float(ov), ox)
+
+
+def test_batched_auto_falls_back_when_fp32_windows_overflow():
+    """The instance of tests/test_gpu_mix.py whose small terms vanish in the
+    2^23 image (2^25 states inside the window) overflows the batch's
+    candidate buffer on the two-pipe pass; AUTO repeats the batch on the int32
+    pass and still certifies every instance."""
+    n = 26
+    Q = np.zeros((n, n))
+    Q[0, 0] = -1.0
+    for i in range(1, n):
+        Q[i, i] = -5e-8 * (1.0 + i / 100.0)
+    other = np.random.default_rng(3).normal(size=(20, 20)).astype(np.float32)
+    dQs = to_dev([other, Q])
+    with pytest.raises(qb.QbfError) as e:
+        qb.solve_batched(dQs, variant=qb.QBF_VARIANT_SPLIT_MIX)
+    assert e.value.status == qb.QBF_EOVERFLOW
+    vmin, am = qb.solve_batched(dQs)
+    assert (vmin[1], am[1]) == oracle.brute_min(Q)
+    assert am[1] == (1 << n) - 1
+    assert (vmin[0], am[0]) == oracle.brute_min(other)
