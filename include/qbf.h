@@ -99,7 +99,7 @@ typedef struct {
     int timing;         /* 1: time the main walk kernel with CUDA events on
                            `stream` and report it in qbf_result.walk_seconds */
     int batch_suffix_bits; /* qbf_solve_batched: suffix bits walked per lane,
-                              6..16; 0 = the autotuned value (default 14)  */
+                              6..18; 0 = the autotuned value (default 16)  */
     int reserved[6];
 } qbf_options;
 
@@ -257,7 +257,7 @@ int qbf_solve_batched(const void *const *Q_dev, const int *n, const int *dtype, 
  * qbf_tune_batched -- picks the per-lane suffix width of qbf_solve_batched.
  *
  * Times qbf_solve_batched on the given batch for every suffix width in
- * [6, 16] between lo_bits and hi_bits, keeps the fastest as this process's
+ * [6, 18] between lo_bits and hi_bits, keeps the fastest as this process's
  * default for the current device and returns it in *best_bits (and its time
  * in *best_seconds).  If the environment variable QBF_TUNE_CACHE names a file,
  * a line "<device name> <SM count> <bits> <seconds>" is appended to it.

@@ -910,9 +910,9 @@ int qbf_tune_batched(const void *const *Q_dev, const int *n, const int *dtype, i
     if (!best_bits || !best_seconds)
         return set_err(QBF_EINVAL, "null pointer argument");
     lo_bits = std::max(lo_bits, kRMax);
-    hi_bits = std::min(hi_bits, 16);
+    hi_bits = std::min(hi_bits, 18);
     if (lo_bits > hi_bits)
-        return set_err(QBF_EINVAL, "empty suffix-width range (valid: 6..16)");
+        return set_err(QBF_EINVAL, "empty suffix-width range (valid: 6..18)");
     cudaStream_t s = (cudaStream_t)stream;
     std::vector<double> vmin(count);
     std::vector<uint64_t> am(count);

@@ -42,7 +42,7 @@ namespace {
 constexpr int kBatchThreads = 128;
 constexpr int kBatchWarps = kBatchThreads / 32;
 constexpr int kBatchR = kRMax;
-constexpr int kBatchMaxNS = 16;
+constexpr int kBatchMaxNS = 18;
 constexpr int kBatchMinN = 11;  // smallest walk dimension: ns >= R and 32 prefixes per item
 // per warp: the 16-byte correction records of the two-pipe walk (128 x int4,
 // first so they stay 16-byte aligned), then S, lin, K and the lane parts of
@@ -550,9 +550,9 @@ int solve_batched_mode(const void *const *Q, const int *n, const int *dtype, int
     if ((int)g_bstate.size() <= dev)
         g_bstate.resize(dev + 1);
     BatchState &B = g_bstate[dev];
-    int NS = o.batch_suffix_bits > 0 ? o.batch_suffix_bits : (B.tuned_ns > 0 ? B.tuned_ns : 14);
+    int NS = o.batch_suffix_bits > 0 ? o.batch_suffix_bits : (B.tuned_ns > 0 ? B.tuned_ns : 16);
     if (NS < kBatchR || NS > kBatchMaxNS)
-        return record_error(QBF_EINVAL, "batch_suffix_bits must be in [6, 16]");
+        return record_error(QBF_EINVAL, "batch_suffix_bits must be in [6, 18]");
 
     // plan every instance
     std::vector<BatchDesc> desc(count);

@@ -35,7 +35,7 @@ def test_batched_small_mixed_against_oracle():
         assert (vmin[i], am[i]) == (float(v), a), i
 
 
-@pytest.mark.parametrize("bits", [6, 9, 14, 16])
+@pytest.mark.parametrize("bits", [6, 9, 14, 16, 18])
 def test_batched_suffix_width_does_not_change_answer(bits):
     Qs = [inputs.uniform_int(int(n), seed=int(n), lo=-5, hi=5) for n in (11, 14, 17, 20, 22)]
     Qs += [inputs.gaussian_f32(int(n), seed=int(n)) for n in (12, 19, 21)]
