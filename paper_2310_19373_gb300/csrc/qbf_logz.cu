@@ -31,6 +31,7 @@
 #include <cstring>
 #include <mutex>
 #include <string>
+#include <type_traits>
 #include <vector>
 
 #include "qbf.h"
@@ -78,8 +79,21 @@ __device__ __forceinline__ void kahan_add(float &s, float &c, float x)
     s = t;
 }
 
-// Two int32 walks (hi and lo limb) over the same suffix in lockstep; visit is
-// called at every state, flush after every block of 2^R states.
+// compile-time loop: f(std::integral_constant<int, I>) for I = B .. E-1
+template <int B, int E, class F>
+__device__ __forceinline__ void static_for(F &&f)
+{
+    if constexpr (B < E) {
+        f(std::integral_constant<int, B>{});
+        static_for<B + 1, E>(f);
+    }
+}
+
+// Two int32 walks (hi and lo limb) over the same suffix in lockstep.
+// visit(vh, vl, U, pi) is called at every state, with U the compile-time step
+// in the block (0 for the block's first state) and pi the block parity; the
+// low R bits of the state's Gray code are then gray(U), except bit R - 1,
+// which is gray(U)'s bit R - 1 xor pi.  flush(B) follows every block B.
 template <int R, class F, class G>
 __device__ __forceinline__ void walk2(unsigned vh, unsigned (&GLh)[R], unsigned vl,
                                       unsigned (&GLl)[R], int ns, const int4 *rh, const int4 *rl,
@@ -88,7 +102,6 @@ __device__ __forceinline__ void walk2(unsigned vh, unsigned (&GLh)[R], unsigned 
 {
     const int M = ns - R;
     const unsigned nblocks = 1u << M;
-    visit(vh, vl, 0u);
     for (unsigned B = 0; B < nblocks; ++B) {
         const int pi = B & 1;
         if (B > 0) {
@@ -96,7 +109,6 @@ __device__ __forceinline__ void walk2(unsigned vh, unsigned (&GLh)[R], unsigned 
             const int4 al = __ldg(rl + 2 * B), bl = __ldg(rl + 2 * B + 1);
             vh = vh + (unsigned)ah.x + (unsigned)sCh[ah.y * stride + slot];
             vl = vl + (unsigned)al.x + (unsigned)sCl[al.y * stride + slot];
-            visit(vh, vl, B << R);
             const int Wh[6] = {ah.z, ah.w, bh.x, bh.y, bh.z, bh.w};
             const int Wl[6] = {al.z, al.w, bl.x, bl.y, bl.z, bl.w};
 #pragma unroll
@@ -105,20 +117,21 @@ __device__ __forceinline__ void walk2(unsigned vh, unsigned (&GLh)[R], unsigned 
                 GLl[i] += (unsigned)Wl[i];
             }
         }
-#pragma unroll
-        for (int u = 1; u < (1 << R); ++u) {
-            const int l = ctz_c(u);
-            const int g = u ^ (u >> 1);
+        visit(vh, vl, std::integral_constant<int, 0>{}, pi);
+        static_for<1, (1 << R)>([&](auto U) {
+            constexpr int u = decltype(U)::value;
+            constexpr int l = ctz_c(u);
+            constexpr int g = u ^ (u >> 1);
             const int nb = ((g >> l) & 1) ^ ((l == R - 1) ? pi : 0);
             vh = vh + (nb ? GLh[l] : 0u - GLh[l]) + (unsigned)Kh[pi * 64 + u];
             vl = vl + (nb ? GLl[l] : 0u - GLl[l]) + (unsigned)Kl[pi * 64 + u];
-            visit(vh, vl, (B << R) | (unsigned)u);
-        }
-        flush();
+            visit(vh, vl, U, pi);
+        });
+        flush(B);
     }
 }
 
-template <int R, int MODE>
+template <int R, int MODE, int NB>
 __global__ void __launch_bounds__(kLzThreads) logz_walk_kernel(LzArgs a)
 {
     extern __shared__ int sm[];
@@ -159,58 +172,83 @@ __global__ void __launch_bounds__(kLzThreads) logz_walk_kernel(LzArgs a)
     const int4 *rl = reinterpret_cast<const int4 *>(a.recs + (size_t)(pidx + 1) * a.rec_stride);
 
     if constexpr (MODE == kModeZ) {
-        float acc[kLzMaxBeta], sum[kLzMaxBeta], comp[kLzMaxBeta];
+        // NB betas (exactly a.nbeta for NB <= 4; up to NB = 8 with the rest
+        // predicated off), each an FP32 block sum flushed into a Kahan sum
+        constexpr bool exact_nb = NB <= 4;
+        float acc[NB], sum[NB], comp[NB], ch[NB], cl[NB];
 #pragma unroll
-        for (int j = 0; j < kLzMaxBeta; ++j)
+        for (int j = 0; j < NB; ++j) {
             acc[j] = sum[j] = comp[j] = 0.f;
+            ch[j] = a.ch[j];
+            cl[j] = a.cl[j];
+        }
         walk2<R>(vh, GLh, vl, GLl, ns, rh, rl, sCh, sCl, kLzThreads, threadIdx.x, sKh, sKl,
-                 [&](unsigned xh, unsigned xl, unsigned) {
+                 [&](unsigned xh, unsigned xl, auto, int) {
                      const float dh = (float)(int)(xh - mh), dl = (float)(int)(xl - ml);
 #pragma unroll
-                     for (int j = 0; j < kLzMaxBeta; ++j)
-                         if (j < a.nbeta)
-                             acc[j] += ex2_approx(fmaf(dh, a.ch[j], dl * a.cl[j]));
+                     for (int j = 0; j < NB; ++j)
+                         if (exact_nb || j < a.nbeta)
+                             acc[j] += ex2_approx(fmaf(dh, ch[j], dl * cl[j]));
                  },
-                 [&]() {
+                 [&](unsigned) {
 #pragma unroll
-                     for (int j = 0; j < kLzMaxBeta; ++j) {
+                     for (int j = 0; j < NB; ++j) {
                          kahan_add(sum[j], comp[j], acc[j]);
                          acc[j] = 0.f;
                      }
                  });
         if (active) {
 #pragma unroll
-            for (int j = 0; j < kLzMaxBeta; ++j)
-                if (j < a.nbeta)
+            for (int j = 0; j < NB; ++j)
+                if (exact_nb || j < a.nbeta)
                     a.laneZ[((size_t)b * a.lanes + p) * a.nbeta + j] =
                         (double)sum[j] - (double)comp[j];
         }
     } else {
-        float acc0 = 0.f, sum0 = 0.f, comp0 = 0.f;
-        float acc[kLzMaxNs], sum[kLzMaxNs], comp[kLzMaxNs];
+        // Z and M1[j] = sum of w over the states with suffix bit j set.  Bits
+        // below R - 1 are compile-time per step, bit R - 1 depends on the
+        // block parity, bits >= R are constant over a block: they take the
+        // block total at the flush.
+        float acc0 = 0.f, sum0 = 0.f, comp0 = 0.f, accTop = 0.f;
+        float accLo[R > 1 ? R - 1 : 1];
+        float sum[kLzMaxNs], comp[kLzMaxNs];
 #pragma unroll
         for (int j = 0; j < kLzMaxNs; ++j)
-            acc[j] = sum[j] = comp[j] = 0.f;
+            sum[j] = comp[j] = 0.f;
+#pragma unroll
+        for (int j = 0; j < (R > 1 ? R - 1 : 1); ++j)
+            accLo[j] = 0.f;
         const float ch = a.ch[0], cl = a.cl[0];
         walk2<R>(vh, GLh, vl, GLl, ns, rh, rl, sCh, sCl, kLzThreads, threadIdx.x, sKh, sKl,
-                 [&](unsigned xh, unsigned xl, unsigned t) {
+                 [&](unsigned xh, unsigned xl, auto U, int pi) {
+                     constexpr int u = decltype(U)::value;
+                     constexpr int g = u ^ (u >> 1);
                      const float dh = (float)(int)(xh - mh), dl = (float)(int)(xl - ml);
                      const float w = ex2_approx(fmaf(dh, ch, dl * cl));
-                     const unsigned g = t ^ (t >> 1);
                      acc0 += w;
-#pragma unroll
-                     for (int j = 0; j < kLzMaxNs; ++j)
-                         if (j < ns && ((g >> j) & 1u))
-                             acc[j] += w;
+                     static_for<0, R - 1>([&](auto J) {
+                         if constexpr ((g >> decltype(J)::value) & 1)
+                             accLo[decltype(J)::value] += w;
+                     });
+                     if (((g >> (R - 1)) & 1) ^ pi)
+                         accTop += w;
                  },
-                 [&]() {
+                 [&](unsigned B) {
+                     const float blk = acc0;
                      kahan_add(sum0, comp0, acc0);
                      acc0 = 0.f;
 #pragma unroll
-                     for (int j = 0; j < kLzMaxNs; ++j) {
-                         kahan_add(sum[j], comp[j], acc[j]);
-                         acc[j] = 0.f;
+                     for (int j = 0; j < R - 1; ++j) {
+                         kahan_add(sum[j], comp[j], accLo[j]);
+                         accLo[j] = 0.f;
                      }
+                     kahan_add(sum[R - 1], comp[R - 1], accTop);
+                     accTop = 0.f;
+                     const unsigned gB = B ^ (B >> 1);
+#pragma unroll
+                     for (int j = R; j < kLzMaxNs; ++j)
+                         if (j < ns && ((gB >> (j - R)) & 1u))
+                             kahan_add(sum[j], comp[j], blk);
                  });
         if (active) {
             a.laneZ[(size_t)b * a.lanes + p] = (double)sum0 - (double)comp0;
@@ -293,57 +331,87 @@ __global__ void __launch_bounds__(256) logz_reduce_kernel(const Plan *plans, con
 }
 
 // E[x_i x_j] for one beta from walk A (Z, M1) and walk B (Z); adds
-// up[b] * (-beta) * E into grad and optionally stores E.
+// up[b] * (-beta) * E into grad and optionally stores E.  One block per
+// (instance b, row i): every thread accumulates its share of the lanes for
+// every j >= i in registers, then each column is reduced by a fixed tree, so
+// the sums do not depend on scheduling.
 __global__ void __launch_bounds__(256) logz_moments_kernel(
     int n, int nsA, unsigned long long lanesA, unsigned long long lanesB, const double *ZA,
-    const double *M1A, const double *ZB, double beta, const double *up, int up_stride,
-    int up_off, double *grad, double *moment, int moment_stride, int moment_off)
+    const double *M1A, const double *ZB, int zb_stride, int zb_off, double beta,
+    const double *up, int up_stride, int up_off, double *grad, double *moment,
+    int moment_stride, int moment_off)
 {
     __shared__ double red[256];
-    const int b = blockIdx.x;
+    const int b = blockIdx.x / n, i = blockIdx.x % n;
     const double *za = ZA + (size_t)b * lanesA;
     const double *m1 = M1A + (size_t)b * lanesA * nsA;
-    const double *zb = ZB + (size_t)b * lanesB;
+    const double *zb = ZB + (size_t)b * lanesB * zb_stride + zb_off;  // beta column
+    double acc[QBF_BATCH_MAX_N];
+#pragma unroll
+    for (int j = 0; j < QBF_BATCH_MAX_N; ++j)
+        acc[j] = 0.0;
+    if (i >= nsA) {
+        // both top: prefix bits of walk A
+        const int bi = i - nsA;
+        for (unsigned long long p = threadIdx.x; p < lanesA; p += blockDim.x) {
+            if (!((p >> bi) & 1ull))
+                continue;
+            const double z = __ldg(za + p);
+#pragma unroll
+            for (int j = 0; j < QBF_BATCH_MAX_N; ++j)
+                if (j >= i && j < n && ((p >> (j - nsA)) & 1ull))
+                    acc[j] += z;
+        }
+    } else {
+        // i bottom, j bottom: prefix bits i, j of walk B
+        for (unsigned long long p = threadIdx.x; p < lanesB; p += blockDim.x) {
+            if (!((p >> i) & 1ull))
+                continue;
+            const double z = __ldg(zb + p * zb_stride);
+#pragma unroll
+            for (int j = 0; j < QBF_BATCH_MAX_N; ++j)
+                if (j >= i && j < nsA && ((p >> j) & 1ull))
+                    acc[j] += z;
+        }
+        // i bottom, j top: walk A's first moments of bit i
+        for (unsigned long long p = threadIdx.x; p < lanesA; p += blockDim.x) {
+            const double v = __ldg(m1 + p * nsA + i);
+#pragma unroll
+            for (int j = 0; j < QBF_BATCH_MAX_N; ++j)
+                if (j >= nsA && j < n && ((p >> (j - nsA)) & 1ull))
+                    acc[j] += v;
+        }
+    }
     const double ZAt = block_sum_fixed(za, lanesA, 1, red);
-    const double ZBt = block_sum_fixed(zb, lanesB, 1, red);
+    const double ZBt = block_sum_fixed(zb, lanesB, zb_stride, red);
     const double u = up ? up[b * up_stride + up_off] : 1.0;
-    const int npair = n * (n + 1) / 2;
-    for (int e = threadIdx.x; e < npair; e += blockDim.x) {
-        // e -> (i, j), i <= j
-        int i = 0, rem = e;
-        while (rem >= n - i) {
-            rem -= n - i;
-            ++i;
+#pragma unroll 1
+    for (int j = i; j < n; ++j) {
+        double v = 0.0;
+#pragma unroll
+        for (int jj = 0; jj < QBF_BATCH_MAX_N; ++jj)
+            if (jj == j)
+                v = acc[jj];
+        red[threadIdx.x] = v;
+        __syncthreads();
+        for (int o = blockDim.x / 2; o > 0; o >>= 1) {
+            if (threadIdx.x < o)
+                red[threadIdx.x] += red[threadIdx.x + o];
+            __syncthreads();
         }
-        const int j = i + rem;
-        double s = 0.0, E;
-        if (i >= nsA) {  // both top: prefix bits of walk A
-            const int bi = i - nsA, bj = j - nsA;
-            for (unsigned long long p = 0; p < lanesA; ++p)
-                if (((p >> bi) & 1ull) && ((p >> bj) & 1ull))
-                    s += za[p];
-            E = s / ZAt;
-        } else if (j >= nsA) {  // i bottom, j top
-            const int bj = j - nsA;
-            for (unsigned long long p = 0; p < lanesA; ++p)
-                if ((p >> bj) & 1ull)
-                    s += m1[p * nsA + i];
-            E = s / ZAt;
-        } else {  // both bottom: prefix bits i, j of walk B
-            for (unsigned long long p = 0; p < lanesB; ++p)
-                if (((p >> i) & 1ull) && ((p >> j) & 1ull))
-                    s += zb[p];
-            E = s / ZBt;
+        if (threadIdx.x == 0) {
+            const double E = red[0] / ((i < nsA && j < nsA) ? ZBt : ZAt);
+            const double gval = u * (-beta) * E;
+            grad[(size_t)b * n * n + i * n + j] += gval;
+            if (i != j)
+                grad[(size_t)b * n * n + j * n + i] += gval;
+            if (moment) {
+                double *mm = moment + (size_t)b * moment_stride + moment_off;
+                mm[i * n + j] = E;
+                mm[j * n + i] = E;
+            }
         }
-        const double gval = u * (-beta) * E;
-        grad[(size_t)b * n * n + i * n + j] += gval;
-        if (i != j)
-            grad[(size_t)b * n * n + j * n + i] += gval;
-        if (moment) {
-            double *mm = moment + (size_t)b * moment_stride + moment_off;
-            mm[i * n + j] = E;
-            mm[j * n + i] = E;
-        }
+        __syncthreads();
     }
 }
 
@@ -424,7 +492,7 @@ LzLayout lz_layout(const LzGeo &g, int batch, int nbeta)
     L.argmin = take(sizeof(unsigned long long) * batch);
     L.laneZA = take(sizeof(double) * g.lanesA * batch * std::max(nbeta, 1));
     L.laneM1 = take(sizeof(double) * g.lanesA * batch * g.nsA);
-    L.laneZB = take(sizeof(double) * g.lanesB * batch);
+    L.laneZB = take(sizeof(double) * g.lanesB * batch * std::max(nbeta, 1));
     L.beta = take(sizeof(double) * kLzMaxBeta);
     L.total = o;
     return L;
@@ -450,8 +518,8 @@ int lz_pool(size_t bytes, char **base)
     return QBF_OK;
 }
 
-template <int MODE>
-cudaError_t launch_lz(int R, const LzArgs &a, int batch, cudaStream_t s)
+template <int MODE, int NB>
+cudaError_t launch_lz_nb(int R, const LzArgs &a, int batch, cudaStream_t s)
 {
     const size_t smem =
         sizeof(int) * (2 * a.n * a.n + 2 * a.n + 256 + 2 * 2 * (a.ns - R) * kLzThreads);
@@ -466,12 +534,29 @@ cudaError_t launch_lz(int R, const LzArgs &a, int batch, cudaStream_t s)
         return cudaGetLastError();
     };
     switch (R) {
-    case 1: return go(logz_walk_kernel<1, MODE>);
-    case 2: return go(logz_walk_kernel<2, MODE>);
-    case 3: return go(logz_walk_kernel<3, MODE>);
-    case 4: return go(logz_walk_kernel<4, MODE>);
-    case 5: return go(logz_walk_kernel<5, MODE>);
-    default: return go(logz_walk_kernel<6, MODE>);
+    case 1: return go(logz_walk_kernel<1, MODE, NB>);
+    case 2: return go(logz_walk_kernel<2, MODE, NB>);
+    case 3: return go(logz_walk_kernel<3, MODE, NB>);
+    case 4: return go(logz_walk_kernel<4, MODE, NB>);
+    case 5: return go(logz_walk_kernel<5, MODE, NB>);
+    default: return go(logz_walk_kernel<6, MODE, NB>);
+    }
+}
+
+// the moment walk takes one beta; the Z walk is compiled per beta count
+template <int MODE>
+cudaError_t launch_lz(int R, const LzArgs &a, int batch, cudaStream_t s)
+{
+    if constexpr (MODE == kModeM1) {
+        return launch_lz_nb<MODE, 1>(R, a, batch, s);
+    } else {
+        switch (a.nbeta) {
+        case 1: return launch_lz_nb<MODE, 1>(R, a, batch, s);
+        case 2: return launch_lz_nb<MODE, 2>(R, a, batch, s);
+        case 3: return launch_lz_nb<MODE, 3>(R, a, batch, s);
+        case 4: return launch_lz_nb<MODE, 4>(R, a, batch, s);
+        default: return launch_lz_nb<MODE, kLzMaxBeta>(R, a, batch, s);  // 5..8, predicated
+        }
     }
 }
 
@@ -639,7 +724,7 @@ int logz_backward(const void *Q, int n, int dtype, int batch, const double *beta
         return record_error(QBF_EINVAL, "null pointer argument");
     std::lock_guard<std::mutex> lk(g_lmu);
     const LzGeo g = lz_geo(n);
-    const LzLayout L = lz_layout(g, batch, 1);
+    const LzLayout L = lz_layout(g, batch, nbeta);
     char *base = nullptr;
     if ((rc = lz_pool(L.total, &base)))
         return rc;
@@ -651,33 +736,47 @@ int logz_backward(const void *Q, int n, int dtype, int batch, const double *beta
     if ((rc = lz_sigmas((const Plan *)(base + L.plans), batch, sig, s)))
         return rc;
     L_CUDA(cudaMemsetAsync(grad, 0, sizeof(double) * batch * n * n, s), "grad clear");
+    // walk B (rotated variables) needs only Z: one pass for every beta
+    for (int b = 0; b < batch;) {
+        int b1 = b;
+        while (b1 + 1 < batch && sig[b1 + 1] == sig[b])
+            ++b1;
+        LzArgs a = lz_args(g, base, L, 1, nbeta, beta, 0);
+        for (int j = 0; j < nbeta; ++j) {
+            const double c = -beta[j] * 1.4426950408889634 * ldexp(1.0, -sig[b]);
+            a.ch[j] = (float)c;
+            a.cl[j] = (float)(c * ldexp(1.0, -16));
+        }
+        a.plans += (size_t)b * 4;
+        a.K += (size_t)b * 4 * 128;
+        a.recs += (size_t)b * 4 * g.rec_stride;
+        a.shift += (size_t)b * 4;
+        a.laneZ += (size_t)b * a.lanes * nbeta;
+        L_CUDA(launch_lz<kModeZ>(a.R, a, b1 - b + 1, s), "log Z walk (rotated)");
+        b = b1 + 1;
+    }
     for (int j = 0; j < nbeta; ++j) {
         for (int b = 0; b < batch;) {
             int b1 = b;
             while (b1 + 1 < batch && sig[b1 + 1] == sig[b])
                 ++b1;
             const double c = -beta[j] * 1.4426950408889634 * ldexp(1.0, -sig[b]);
-            for (int walk = 0; walk < 2; ++walk) {
-                LzArgs a = lz_args(g, base, L, walk, 1, beta, 0);
-                a.ch[0] = (float)c;
-                a.cl[0] = (float)(c * ldexp(1.0, -16));
-                a.plans += (size_t)b * 4;
-                a.K += (size_t)b * 4 * 128;
-                a.recs += (size_t)b * 4 * g.rec_stride;
-                a.shift += (size_t)b * 4;
-                a.laneZ += (size_t)b * a.lanes;
-                a.laneM1 += (size_t)b * a.lanes * g.nsA;
-                if (walk == 0)
-                    L_CUDA(launch_lz<kModeM1>(a.R, a, b1 - b + 1, s), "log Z moment walk");
-                else
-                    L_CUDA(launch_lz<kModeZ>(a.R, a, b1 - b + 1, s), "log Z walk (rotated)");
-            }
+            LzArgs a = lz_args(g, base, L, 0, 1, beta, 0);
+            a.ch[0] = (float)c;
+            a.cl[0] = (float)(c * ldexp(1.0, -16));
+            a.plans += (size_t)b * 4;
+            a.K += (size_t)b * 4 * 128;
+            a.recs += (size_t)b * 4 * g.rec_stride;
+            a.shift += (size_t)b * 4;
+            a.laneZ += (size_t)b * a.lanes;
+            a.laneM1 += (size_t)b * a.lanes * g.nsA;
+            L_CUDA(launch_lz<kModeM1>(a.R, a, b1 - b + 1, s), "log Z moment walk");
             b = b1 + 1;
         }
-        logz_moments_kernel<<<batch, 256, 0, s>>>(
+        logz_moments_kernel<<<batch * n, 256, 0, s>>>(
             n, g.nsA, g.lanesA, g.lanesB, (const double *)(base + L.laneZA),
-            (const double *)(base + L.laneM1), (const double *)(base + L.laneZB), beta[j],
-            upstream, nbeta, j, grad, moment, nbeta * n * n, j * n * n);
+            (const double *)(base + L.laneM1), (const double *)(base + L.laneZB), nbeta, j,
+            beta[j], upstream, nbeta, j, grad, moment, nbeta * n * n, j * n * n);
         L_CUDA(cudaGetLastError(), "log Z moments");
     }
     L_CUDA(cudaStreamSynchronize(s), "log Z backward");
