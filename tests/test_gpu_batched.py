@@ -87,6 +87,17 @@ def test_batched_config_4096():
     for i in small + mid:
         v, a = oracle.brute_min(Qs[i])
         assert (vmin[i], am[i]) == (float(v), a), i
+    # the largest instances (n >= 32, too large to enumerate here): the 2^20-state
+    # window of natural indices around the reported argmin gives exactly
+    # (min, argmin), and two random windows do no better
+    big = [i for i in range(len(Qs)) if ns[i] >= 32][:12]
+    for i in big:
+        lo = (am[i] >> 20) << 20
+        v, a = oracle.brute_min(Qs[i], lo, lo + (1 << 20))
+        assert (vmin[i], am[i]) == (float(v), a), i
+        for w in rng.integers(0, 1 << (int(ns[i]) - 20), size=2):
+            v, _ = oracle.brute_min(Qs[i], int(w) << 20, (int(w) + 1) << 20)
+            assert float(v) >= vmin[i], i
 
 
 def test_batched_tuner_and_repeat():
