@@ -231,6 +231,19 @@ int qbf_solve_ising(const void *J_dev, const void *h_dev, int n, int dtype,
                     const qbf_options *opt, qbf_result *out, void *stream);
 
 /*
+ * qubo_bf_solve -- the one-call form: minimum, lowest-index argmin and
+ * optionally the top-k of x^T Q x (Eq. 1) for Q in HOST memory, n*n elements
+ * of `dtype`, row-major.  Synchronous on the default stream, default options
+ * (AUTO variant).  min_value and argmin receive the minimum and its natural
+ * index (bit i = x_i).  top_k may be 0 (then topk_value / topk_index may be
+ * NULL); otherwise up to 64 best states are written to the caller's arrays of
+ * that length, and the number written is returned through *count (may be NULL).
+ * Same status codes as qbf_solve.
+ */
+int qubo_bf_solve(const void *Q_host, int n, int dtype, double *min_value, uint64_t *argmin,
+                  int top_k, double *topk_value, uint64_t *topk_index, int *count);
+
+/*
  * qbf_solve_batched -- minimum and lowest-index argmin of many independent QUBOs.
  *
  * Section 3.1's prefix split applied across instances: the prefixes of all

@@ -112,6 +112,10 @@ _SIGS = {
                                          ctypes.POINTER(QbfCheckpoint)]),
     "qbf_chunked_result": (ctypes.c_int, [ctypes.POINTER(QbfCheckpoint),
                                           ctypes.POINTER(QbfResult)]),
+    "qubo_bf_solve": (ctypes.c_int, [_VP, ctypes.c_int, ctypes.c_int,
+                                     ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_uint64),
+                                     ctypes.c_int, ctypes.POINTER(ctypes.c_double),
+                                     ctypes.POINTER(ctypes.c_uint64), ctypes.POINTER(ctypes.c_int)]),
     "qbf_solve_ising": (ctypes.c_int, [_VP, _VP, ctypes.c_int, ctypes.c_int,
                                        ctypes.POINTER(QbfOptions), ctypes.POINTER(QbfResult), _VP]),
     "qbf_solve_batched": (ctypes.c_int, [ctypes.POINTER(ctypes.c_void_p), ctypes.POINTER(ctypes.c_int),
@@ -205,6 +209,26 @@ def qbf_solve_ising(J_dev: int, h_dev: int, n: int, dtype: int, opt: QbfOptions 
                                ctypes.byref(out), _VP(stream or 0))
     _check(rc)
     return out
+
+
+def qubo_bf_solve(Q, top_k: int = 0):
+    """The one-call form for a host matrix (numpy array or CPU tensor): returns
+    (min_value, argmin, [(value, index), ...] of the top_k best states)."""
+    import numpy as np
+
+    a = np.ascontiguousarray(Q.numpy() if hasattr(Q, "numpy") else Q)
+    if a.ndim != 2 or a.shape[0] != a.shape[1]:
+        raise QbfError(QBF_EINVAL, "Q must be a square matrix")
+    codes = {np.dtype(np.float64): QBF_F64, np.dtype(np.float32): QBF_F32,
+             np.dtype(np.int32): QBF_I32, np.dtype(np.int16): QBF_I16}
+    if a.dtype not in codes:
+        raise QbfError(QBF_EDTYPE, f"unsupported dtype {a.dtype}")
+    vmin, am, cnt = ctypes.c_double(), ctypes.c_uint64(), ctypes.c_int()
+    tv = (ctypes.c_double * max(top_k, 1))()
+    ti = (ctypes.c_uint64 * max(top_k, 1))()
+    _check(lib().qubo_bf_solve(_VP(a.ctypes.data), a.shape[0], codes[a.dtype], ctypes.byref(vmin),
+                               ctypes.byref(am), top_k, tv, ti, ctypes.byref(cnt)))
+    return vmin.value, int(am.value), [(tv[i], int(ti[i])) for i in range(cnt.value)]
 
 
 def qbf_chunked_init(ck: QbfCheckpoint, Q_dev: int, n: int, dtype: int, top_k: int,

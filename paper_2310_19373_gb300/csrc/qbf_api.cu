@@ -620,6 +620,37 @@ int qbf_solve_ising(const void *J_dev, const void *h_dev, int n, int dtype,
     return QBF_OK;
 }
 
+int qubo_bf_solve(const void *Q_host, int n, int dtype, double *min_value, uint64_t *argmin,
+                  int top_k, double *topk_value, uint64_t *topk_index, int *count)
+{
+    if (!Q_host || !min_value || !argmin)
+        return set_err(QBF_EINVAL, "null pointer argument");
+    if (top_k < 0 || top_k > QBF_MAX_TOPK)
+        return set_err(QBF_EINVAL, "top_k must be in [0, 64]");
+    if (top_k > 0 && (!topk_value || !topk_index))
+        return set_err(QBF_EINVAL, "null top-k output");
+    qbf_options o;
+    qbf_default_options(&o);
+    o.top_k = top_k > 0 ? top_k : 1;
+    qbf_result r;
+    int rc;
+    {
+        std::lock_guard<std::mutex> lk(g_mu);
+        rc = solve_locked(Q_host, true, n, dtype, &o, &r, (cudaStream_t)0);
+    }
+    if (rc)
+        return rc;
+    *min_value = r.min_value;
+    *argmin = r.argmin;
+    for (int i = 0; i < top_k && i < r.top_k; ++i) {
+        topk_value[i] = r.topk_value[i];
+        topk_index[i] = r.topk_index[i];
+    }
+    if (count)
+        *count = top_k > 0 ? std::min(top_k, r.top_k) : 0;
+    return QBF_OK;
+}
+
 int qbf_chunked_init(qbf_checkpoint *ck, const void *Q_dev, int n, int dtype, int top_k,
                      int chunk_bits, int shard, int nshards, void *stream)
 {

@@ -16,7 +16,7 @@ HEADER = os.path.join(ROOT, "include", "qbf.h")
 def declared_functions():
     text = open(HEADER).read()
     text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
-    return sorted(set(re.findall(r"\b(qbf_[a-z0-9_]+)\s*\(", text)))
+    return sorted(set(re.findall(r"\b(q(?:bf|ubo_bf)_[a-z0-9_]+)\s*\(", text)))
 
 
 @pytest.fixture(scope="module")

@@ -258,3 +258,28 @@ def test_host_pointer_path_matches_device_path():
     a = qb.solve(dev(Q), top_k=8)
     b = qb.solve(torch.from_numpy(Q), top_k=8)
     assert a.topk_indices == b.topk_indices and a.topk_values == b.topk_values
+
+
+def test_qubo_bf_solve_one_call_form():
+    """qubo_bf_solve(Q_host, n, dtype) -> min, argmin, optional top-k."""
+    g = json.load(open(os.path.join(GOLDEN, "hand_n3.json")))
+    Q = np.array(g["Q"], dtype=np.float64)
+    v, x, top = qb.qubo_bf_solve(Q, top_k=3)
+    assert (v, x) == (-2.0, 1)
+    assert top == [(-2.0, 1), (-2.0, 3), (-2.0, 6)]
+    Q20 = inputs.config_n20_f64(0)
+    vals, ix = oracle.brute_topk(Q20, 8)
+    v, x, top = qb.qubo_bf_solve(Q20, top_k=8)
+    assert (v, x) == (float(vals[0]), int(ix[0]))
+    assert top == [(float(a), int(b)) for a, b in zip(vals, ix)]
+    Qi = np.random.default_rng(4).integers(-30, 31, size=(15, 15)).astype(np.int16)
+    v, x, top = qb.qubo_bf_solve(Qi)
+    ov, ox = oracle.brute_min(Qi)
+    assert (v, x) == (float(ov), ox)
+    assert top == []
+    with pytest.raises(qb.QbfError) as e:
+        qb.qubo_bf_solve(Q20, top_k=65)
+    assert e.value.status == qb.QBF_EINVAL
+    with pytest.raises(qb.QbfError) as e:
+        qb.qubo_bf_solve(Q20.astype(np.uint8))
+    assert e.value.status == qb.QBF_EDTYPE
