@@ -67,7 +67,7 @@ enum {
 
 /* walk kernels */
 enum {
-    QBF_VARIANT_AUTO = 0,  /* n >= 24: SPLIT_MIX, repeated on SPLIT if its
+    QBF_VARIANT_AUTO = 0,  /* n >= 24: SPLIT_DEFER, repeated on SPLIT if its
                               2^23 image bound does not hold (integer Q) or
                               its wider certification window overflows the
                               candidate buffer (float Q); n < 24: SPLIT     */
@@ -82,9 +82,14 @@ enum {
     QBF_VARIANT_SPLIT_MIX = 5, /* split walk on both pipes: per thread three
                                   packed-FP32 pairs and two int32 prefixes
                                   (image < 2^23, n >= 4)                     */
-    QBF_VARIANT_NAIVE = 6      /* no Gray code: every state evaluated from
+    QBF_VARIANT_NAIVE = 6,     /* no Gray code: every state evaluated from
                                   scratch in natural order, O(n^2) per state;
                                   a reference form, not fast                 */
+    QBF_VARIANT_SPLIT_DEFER = 7 /* split walk, eight prefixes per thread as
+                                   four packed-FP32 pairs, the static in-block
+                                   correction added once per step after the
+                                   minimum over the eight (image < 2^23,
+                                   n >= 4)                                   */
 };
 
 typedef struct {

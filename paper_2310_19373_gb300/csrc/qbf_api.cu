@@ -188,14 +188,14 @@ int plan_geometry(int n, const qbf_options &o, Geo *g)
         } else {
             k = n - std::min(auto_suffix_bits(nf), kFieldMaxSuffix);
         }
-    } else if (o.variant == QBF_VARIANT_SPLIT_MIX) {
+    } else if (o.variant == QBF_VARIANT_SPLIT_MIX || o.variant == QBF_VARIANT_SPLIT_DEFER) {
         // a lane walks nsw bits for all eight values of the group bits nsw..nsw+2
         if (n < 4)
-            return set_err(QBF_EINVAL, "the two-pipe walk needs n >= 4");
+            return set_err(QBF_EINVAL, "the eight-prefix walks need n >= 4");
         if (o.prefix_bits >= 0) {
             k = o.prefix_bits;
             if (k > n - 4 || k > 28)
-                return set_err(QBF_EINVAL, "prefix_bits must be in [0, min(n-4, 28)] for the two-pipe walk");
+                return set_err(QBF_EINVAL, "prefix_bits must be in [0, min(n-4, 28)] for the eight-prefix walks");
         } else {
             const int nsw = std::max(1, std::min(auto_suffix_bits(nf), nf - 3));
             k = n - nsw - 3;
@@ -231,9 +231,9 @@ int plan_geometry(int n, const qbf_options &o, Geo *g)
     g->n = n;
     g->k = k;
     g->ns = n - k;
-    if (o.variant == QBF_VARIANT_SPLIT_MIX) {
+    if (o.variant == QBF_VARIANT_SPLIT_MIX || o.variant == QBF_VARIANT_SPLIT_DEFER) {
         if (g->ns < 4)
-            return set_err(QBF_EINVAL, "fix_bits must be <= n - 4 for the two-pipe walk");
+            return set_err(QBF_EINVAL, "fix_bits must be <= n - 4 for the eight-prefix walks");
         const int nsw = g->ns - 3;
         g->R = std::min(kRMax, nsw);
         g->M = nsw - g->R;
@@ -315,16 +315,17 @@ int solve_one(const void *Q, bool host_q, int n, int dtype, const qbf_options *o
     if (o.variant != QBF_VARIANT_AUTO && o.variant != QBF_VARIANT_SPLIT &&
         o.variant != QBF_VARIANT_TC && o.variant != QBF_VARIANT_SPLIT_F32 &&
         o.variant != QBF_VARIANT_SPLIT_MIX && o.variant != QBF_VARIANT_FIELD &&
-        o.variant != QBF_VARIANT_NAIVE)
+        o.variant != QBF_VARIANT_NAIVE && o.variant != QBF_VARIANT_SPLIT_DEFER)
         return set_err(QBF_ENOTIMPL, "requested walk variant is not built");
     Geo g;
     if ((rc = plan_geometry(n, o, &g)))
         return rc;
     const bool tc = (o.variant == QBF_VARIANT_TC);
     const bool mix = (o.variant == QBF_VARIANT_SPLIT_MIX);
+    const bool defer = (o.variant == QBF_VARIANT_SPLIT_DEFER);
     const bool field = (o.variant == QBF_VARIANT_FIELD);
     const bool naive = (o.variant == QBF_VARIANT_NAIVE);
-    const bool f32 = (o.variant == QBF_VARIANT_SPLIT_F32) || mix;  // same image bound
+    const bool f32 = (o.variant == QBF_VARIANT_SPLIT_F32) || mix || defer;  // same image bound
 
     const unsigned long long npref = g.p_hi - g.p_lo;
     const size_t qbytes = host_q ? dtype_size(dtype) * n * n : 0;
@@ -374,6 +375,10 @@ int solve_one(const void *Q, bool host_q, int n, int dtype, const qbf_options *o
         QBF_CUDA(launch_walk_field(plan, a, num_sms(), s), "walk field (min)");
     else if (naive)
         QBF_CUDA(launch_walk_naive(plan, a, num_sms(), s), "naive (min)");
+    else if (defer)
+        QBF_CUDA(launch_walk_defer(g.R, plan, recs, a, (const int *)(base + L.kbuf),
+                                   base + L.kbuf + sizeof(int) * kKbufInts, num_sms(), s),
+                 "walk defer (min)");
     else if (mix)
         QBF_CUDA(launch_walk_mix(g.R, plan, recs, a, (const int *)(base + L.kbuf),
                                  (unsigned long long *)(base + L.kbuf + sizeof(int) * kKbufInts),
@@ -469,6 +474,7 @@ int solve_one(const void *Q, bool host_q, int n, int dtype, const qbf_options *o
     out->prefix_bits = g.k;
     out->suffix_bits = g.ns;
     out->variant = tc      ? QBF_VARIANT_TC
+                   : defer ? QBF_VARIANT_SPLIT_DEFER
                    : mix   ? QBF_VARIANT_SPLIT_MIX
                    : f32   ? QBF_VARIANT_SPLIT_F32
                    : field ? QBF_VARIANT_FIELD
@@ -482,8 +488,8 @@ int solve_one(const void *Q, bool host_q, int n, int dtype, const qbf_options *o
     return QBF_OK;
 }
 
-// QBF_VARIANT_AUTO with n >= kAutoMixMinN takes the two-pipe walk (the
-// fastest form on this part).  Its image is bounded by 2^23 instead of 2^31:
+// QBF_VARIANT_AUTO with n >= kAutoMixMinN takes the deferred-correction walk
+// (the fastest form on this part).  Its image is bounded by 2^23 instead of 2^31:
 // integer Q with a larger sum |Q_ij| is rejected by prepare (QBF_ERANGE)
 // before any walk work, and for float Q the certification window is 2^8
 // times wider, so if it flags more candidates than the candidate buffer holds
@@ -500,7 +506,7 @@ int solve_locked(const void *Q, bool host_q, int n, int dtype, const qbf_options
     if (o.variant == QBF_VARIANT_AUTO && n >= kAutoMixMinN && o.prefix_bits <= n - 4 &&
         o.fix_bits <= n - 4) {
         qbf_options om = o;
-        om.variant = QBF_VARIANT_SPLIT_MIX;
+        om.variant = QBF_VARIANT_SPLIT_DEFER;
         const int rc = solve_one(Q, host_q, n, dtype, &om, out, s);
         if (rc != QBF_EOVERFLOW && rc != QBF_ERANGE)
             return rc;
@@ -835,7 +841,8 @@ int qbf_prefix_minima(const void *Q_dev, int n, int dtype, int prefix_bits, int 
         return set_err(QBF_EINVAL, "prefix_bits must be given");
     if (variant != QBF_VARIANT_AUTO && variant != QBF_VARIANT_SPLIT && variant != QBF_VARIANT_TC &&
         variant != QBF_VARIANT_SPLIT_F32 && variant != QBF_VARIANT_SPLIT_MIX &&
-        variant != QBF_VARIANT_FIELD && variant != QBF_VARIANT_NAIVE)
+        variant != QBF_VARIANT_FIELD && variant != QBF_VARIANT_NAIVE &&
+        variant != QBF_VARIANT_SPLIT_DEFER)
         return set_err(QBF_ENOTIMPL, "requested walk variant is not built");
     qbf_options o;
     qbf_default_options(&o);
@@ -843,9 +850,10 @@ int qbf_prefix_minima(const void *Q_dev, int n, int dtype, int prefix_bits, int 
     o.variant = variant;
     const bool tc = (variant == QBF_VARIANT_TC);
     const bool mix = (variant == QBF_VARIANT_SPLIT_MIX);
+    const bool defer = (variant == QBF_VARIANT_SPLIT_DEFER);
     const bool field = (variant == QBF_VARIANT_FIELD);
     const bool naive = (variant == QBF_VARIANT_NAIVE);
-    const bool f32 = (variant == QBF_VARIANT_SPLIT_F32) || mix;  // same image bound
+    const bool f32 = (variant == QBF_VARIANT_SPLIT_F32) || mix || defer;  // same image bound
     Geo g;
     int rc = plan_geometry(n, o, &g);
     if (rc)
@@ -874,6 +882,11 @@ int qbf_prefix_minima(const void *Q_dev, int n, int dtype, int prefix_bits, int 
         QBF_CUDA(launch_walk_field(plan, a, num_sms(), s), "walk field (min)");
     else if (naive)
         QBF_CUDA(launch_walk_naive(plan, a, num_sms(), s), "naive (min)");
+    else if (defer)
+        QBF_CUDA(launch_walk_defer(g.R, plan, (const Rec *)(base + L.recs), a,
+                                   (const int *)(base + L.kbuf),
+                                   base + L.kbuf + sizeof(int) * kKbufInts, num_sms(), s),
+                 "walk defer (min)");
     else if (mix)
         QBF_CUDA(launch_walk_mix(g.R, plan, (const Rec *)(base + L.recs), a,
                                  (const int *)(base + L.kbuf),

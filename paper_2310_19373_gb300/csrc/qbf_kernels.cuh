@@ -95,6 +95,12 @@ cudaError_t launch_walk_naive(const Plan *plan, const WalkArgs &a, int num_sms, 
 cudaError_t ising_to_qubo(const void *J, const void *h, int n, int dtype, const void **Q,
                           int *qdtype, double *c_host, int *status_host, cudaStream_t s);
 
+// qbf_walk_defer.cu: MIN walk with the in-block correction added after the
+// minimum over eight prefixes (same image bound and geometry as the two-pipe
+// walk); scratch_dev holds 130 floats
+cudaError_t launch_walk_defer(int R, const Plan *plan, const Rec *recs, const WalkArgs &a,
+                              const int *Kbuf_dev, void *scratch_dev, int num_sms, cudaStream_t s);
+
 // qbf_walk_mix.cu: MIN walk on both pipes (same image bound; eight prefixes per thread)
 cudaError_t launch_walk_mix(int R, const Plan *plan, const Rec *recs, const WalkArgs &a,
                             const int *Kbuf_dev, unsigned long long *Kf2_dev, int num_sms,

@@ -1,4 +1,6 @@
-"""GPU parity of the two-pipe walk (QBF_VARIANT_SPLIT_MIX) against the oracle."""
+"""GPU parity of the eight-prefix walks against the oracle: the two-pipe walk
+(QBF_VARIANT_SPLIT_MIX) and the deferred-correction walk
+(QBF_VARIANT_SPLIT_DEFER), which share their geometry and image bound."""
 import json
 import os
 
@@ -15,6 +17,8 @@ pytestmark = pytest.mark.gpu
 from paper_2310_19373_gb300 import _binding as qb  # noqa: E402
 
 MIX = qb.QBF_VARIANT_SPLIT_MIX
+DEFER = qb.QBF_VARIANT_SPLIT_DEFER
+EIGHT = pytest.mark.parametrize("variant", [MIX, DEFER], ids=["mix", "defer"])
 
 
 def dev(Q):
@@ -35,14 +39,15 @@ def _fixed_point_image(Q, sigma):
 @pytest.mark.parametrize("n,k", [(4, 0), (5, 1), (7, 0), (9, 0), (10, 1), (12, 3), (13, 0),
                                  (15, 6), (16, 9), (18, 4), (20, 7), (22, 10)])
 @pytest.mark.parametrize("kind", ["int", "float"])
-def test_mix_prefix_minima(n, k, kind):
+@EIGHT
+def test_mix_prefix_minima(n, k, kind, variant):
     """Minima per prefix (k prefix bits; the eight groups of a thread are suffix bits)."""
     rng = np.random.default_rng(700 + 7 * n + k)
     if kind == "int":
         Q = rng.integers(-100, 101, size=(n, n)).astype(np.int32)
     else:
         Q = rng.normal(size=(n, n)).astype(np.float32)
-    pm, sigma = qb.prefix_minima(dev(Q), k, MIX)
+    pm, sigma = qb.prefix_minima(dev(Q), k, variant)
     pm = pm.cpu().numpy()
     Qhat = Q.astype(np.int64) if kind == "int" else _fixed_point_image(Q, sigma)
     assert np.abs(np.triu(Qhat)).sum() < 2 ** 23
@@ -51,9 +56,10 @@ def test_mix_prefix_minima(n, k, kind):
     assert pm.tolist() == want
 
 
-def test_mix_minimum_in_each_group():
-    """Put the unique minimum in each of the eight groups in turn (three float
-    pairs, both halves, and the two int32 values)."""
+@EIGHT
+def test_mix_minimum_in_each_group(variant):
+    """Put the unique minimum in each of the eight groups in turn (both halves
+    of every packed pair, and the two int32 values of the two-pipe walk)."""
     n, k = 14, 2
     nsw = n - k - 3
     rng = np.random.default_rng(77)
@@ -64,7 +70,7 @@ def test_mix_minimum_in_each_group():
         for t in range(3):
             Q[nsw + t, nsw + t] = -500 if (b >> t) & 1 else 500
         Q[0, 0] = -500
-        pm, _ = qb.prefix_minima(dev(Q), k, MIX)
+        pm, _ = qb.prefix_minima(dev(Q), k, variant)
         ns = n - k
         want = [oracle.brute_min(Q, p << ns, (p + 1) << ns) for p in range(1 << k)]
         assert pm.cpu().numpy().tolist() == [int(w[0]) for w in want]
@@ -72,63 +78,99 @@ def test_mix_minimum_in_each_group():
 
 
 @pytest.mark.parametrize("n", [4, 5, 8, 11, 14, 17, 21])
-def test_mix_solve_against_oracle(n):
+@EIGHT
+def test_mix_solve_against_oracle(n, variant):
     rng = np.random.default_rng(800 + n)
     for Q, k in ((rng.integers(-100, 101, size=(n, n)).astype(np.int32), 4),
                  (np.triu(rng.uniform(-1, 1, size=(n, n))), 3),
                  (rng.normal(size=(n, n)).astype(np.float32), 2)):
-        sol = qb.solve(dev(Q), top_k=k, variant=MIX)
+        sol = qb.solve(dev(Q), top_k=k, variant=variant)
         vals, ix = oracle.brute_topk(Q, k)
         assert sol.topk_indices == [int(i) for i in ix]
         assert sol.topk_values == [float(v) for v in vals]
-        assert sol.variant == MIX
+        assert sol.variant == variant
 
 
-def test_mix_workloads():
+@EIGHT
+def test_mix_workloads(variant):
     g = json.load(open(os.path.join(GOLDEN, "config_n32_int.json")))["dense"]
-    sol = qb.solve(dev(inputs.config_n32_int(0)), top_k=8, variant=MIX)
+    sol = qb.solve(dev(inputs.config_n32_int(0)), top_k=8, variant=variant)
     assert (int(sol.min_value), sol.argmin) == (g["min"], g["argmin"])
     assert [[int(v), i] for v, i in zip(sol.topk_values, sol.topk_indices)] == g["top8"]
     Q = inputs.config_n40_f32(0)
-    a = qb.solve(dev(Q), variant=MIX)
+    a = qb.solve(dev(Q), variant=variant)
     b = qb.solve(dev(Q), variant=qb.QBF_VARIANT_SPLIT)
     assert (a.min_value, a.argmin) == (b.min_value, b.argmin)
     rng = np.random.default_rng(41)
     for fv in [a.argmin >> 20] + [int(v) for v in rng.integers(0, 1 << 20, size=2)]:
-        s = qb.solve(dev(Q), fix_bits=20, fix_value=fv, variant=MIX)
+        s = qb.solve(dev(Q), fix_bits=20, fix_value=fv, variant=variant)
         assert (s.min_value, s.argmin) == oracle.brute_min(Q, fv << 20, (fv + 1) << 20)
 
 
-def test_mix_errors():
+@EIGHT
+def test_mix_errors(variant):
     with pytest.raises(qb.QbfError) as e:
-        qb.solve(dev(np.zeros((3, 3), dtype=np.float32)), variant=MIX)
+        qb.solve(dev(np.zeros((3, 3), dtype=np.float32)), variant=variant)
     assert e.value.status == qb.QBF_EINVAL
     with pytest.raises(qb.QbfError) as e:
-        qb.prefix_minima(dev(np.zeros((10, 10), dtype=np.float32)), 7, MIX)
+        qb.prefix_minima(dev(np.zeros((10, 10), dtype=np.float32)), 7, variant)
     assert e.value.status == qb.QBF_EINVAL
     with pytest.raises(qb.QbfError) as e:  # sum |Q| >= 2^23: not exact in FP32
-        qb.solve(dev(np.full((12, 12), 200000, dtype=np.int32)), variant=MIX)
+        qb.solve(dev(np.full((12, 12), 200000, dtype=np.int32)), variant=variant)
     assert e.value.status == qb.QBF_ERANGE
 
 
-def test_auto_takes_two_pipe_walk():
-    """AUTO with n >= 24: the two-pipe walk for float Q and for integer Q whose
-    sum |Q| fits the 2^23 image; larger integer Q is repeated on the int32 walk."""
+@pytest.mark.parametrize("n,k", [(12, 0), (15, 2), (19, 5)])
+def test_defer_large_in_block_corrections(n, k):
+    """The deferred walk keeps values without their in-block correction C[u],
+    so |w| reaches |v| + |C|.  Strong couplings among the six unrolled bits
+    (C up to 3e6) against strong fields of the others, with sum |Q| just
+    under 2^23, still give exact minima."""
+    rng = np.random.default_rng(900 + n)
+    Q = np.zeros((n, n), dtype=np.int64)
+    for i in range(6):
+        Q[i, i] = -300000
+        for j in range(i + 1, 6):
+            Q[i, j] = 200000
+    rest = rng.integers(-40000, 40001, size=(n, n))
+    for i in range(n):
+        for j in range(max(i, 6), n):
+            Q[i, j] = rest[i, j]
+    budget = 2 ** 23 - 2 ** 12 - np.abs(Q[:6, :6]).sum()
+    tail = np.abs(Q).sum() - np.abs(Q[:6, :6]).sum()
+    if tail > budget:
+        Q[:, 6:] = Q[:, 6:] * budget // tail
+    Q = Q.astype(np.int32)
+    assert np.abs(Q.astype(np.int64)).sum() < 2 ** 23 - 2 ** 12
+    pm, _ = qb.prefix_minima(dev(Q), k, DEFER)
+    ns = n - k
+    want = [oracle.brute_min(Q, p << ns, (p + 1) << ns)[0] for p in range(1 << k)]
+    assert pm.cpu().numpy().tolist() == want
+    sol = qb.solve(dev(Q), top_k=3, variant=DEFER)
+    vals, ix = oracle.brute_topk(Q, 3)
+    assert sol.topk_indices == [int(i) for i in ix]
+
+
+def test_auto_takes_deferred_walk():
+    """AUTO with n >= 24: the deferred-correction walk for float Q and for
+    integer Q whose sum |Q| fits the 2^23 image; larger integer Q is repeated
+    on the int32 walk."""
     n = 26
     rng = np.random.default_rng(26)
     Qf = np.triu(rng.normal(size=(n, n))).astype(np.float32)
     sol = qb.solve(dev(Qf))
-    assert sol.variant == MIX
+    assert sol.variant == DEFER
     assert (sol.min_value, sol.argmin) == oracle.brute_min(Qf)
     Qi = np.triu(rng.integers(-50, 51, size=(n, n))).astype(np.int32)
     sol = qb.solve(dev(Qi))
-    assert sol.variant == MIX
+    assert sol.variant == DEFER
     assert (int(sol.min_value), sol.argmin) == tuple(int(v) for v in oracle.brute_min(Qi))
     Qb = np.triu(rng.integers(-100000, 100001, size=(n, n))).astype(np.int32)
     assert np.abs(Qb.astype(np.int64)).sum() >= 2 ** 23
-    with pytest.raises(qb.QbfError) as e:
-        qb.solve(dev(Qb), variant=MIX)
-    assert e.value.status == qb.QBF_ERANGE
+    for v in (MIX, DEFER):
+        with pytest.raises(qb.QbfError) as e:
+            qb.solve(dev(Qb), variant=v)
+        assert e.value.status == qb.QBF_ERANGE
     sol = qb.solve(dev(Qb))
     assert sol.variant == qb.QBF_VARIANT_SPLIT
     assert (int(sol.min_value), sol.argmin) == tuple(int(v) for v in oracle.brute_min(Qb))
@@ -148,7 +190,7 @@ def test_auto_falls_back_when_fp32_window_overflows():
     Q[0, 0] = -1.0
     for i in range(1, n):
         Q[i, i] = -5e-8 * (1.0 + i / 100.0)
-    for v in (MIX, qb.QBF_VARIANT_SPLIT_F32):
+    for v in (MIX, DEFER, qb.QBF_VARIANT_SPLIT_F32):
         with pytest.raises(qb.QbfError) as e:
             qb.solve(dev(Q), variant=v)
         assert e.value.status == qb.QBF_EOVERFLOW
