@@ -261,7 +261,12 @@ int qubo_bf_solve(const void *Q_host, int n, int dtype, double *min_value, uint6
  *             elements of dtype[i], row-major.
  * n, dtype  : host arrays of `count` entries; 1 <= n[i] <= QBF_BATCH_MAX_N.
  * opt       : NULL or top_k = 1, fix_bits = 0; batch_suffix_bits selects the
- *             per-lane suffix width (0 = autotuned, see qbf_tune_batched).
+ *             per-lane suffix width (0 = autotuned, see qbf_tune_batched);
+ *             variant AUTO / SPLIT_DEFER (instances whose image fits 2^23
+ *             walk in the deferred-correction form, the rest in int32; AUTO
+ *             repeats the batch on the int32 walk after QBF_EOVERFLOW),
+ *             SPLIT_MIX (the same with the two-pipe form), SPLIT (int32
+ *             throughout); other variants give QBF_ENOTIMPL.
  * min_value, argmin : host arrays of `count` entries (same meaning as
  *             qbf_result.min_value / argmin).
  * 1 <= count <= QBF_BATCH_MAX_COUNT.  Errors name the first failing instance.

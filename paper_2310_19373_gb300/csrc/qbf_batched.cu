@@ -33,6 +33,7 @@
 #include "qbf_internal.cuh"
 #include "qbf_kernels.cuh"
 #include "qbf_walk_core.cuh"
+#include "qbf_walk_defer_core.cuh"
 #include "qbf_walk_mix_core.cuh"
 
 namespace qbf {
@@ -45,8 +46,8 @@ constexpr int kBatchR = kRMax;
 constexpr int kBatchMaxNS = 18;
 constexpr int kBatchMinN = 11;  // smallest walk dimension: ns >= R and 32 prefixes per item
 // per warp: the 16-byte correction records of the two-pipe walk (128 x int4,
-// first so they stay 16-byte aligned), then S, lin, K and the lane parts of
-// the fields
+// first so they stay 16-byte aligned) or the correction sums of the deferred
+// walk (128 floats), then S, lin, K and the lane parts of the fields
 constexpr int kWarpSmemInts =
     (512 + QBF_BATCH_MAX_N * QBF_BATCH_MAX_N + QBF_BATCH_MAX_N + 128 +
      2 * (kBatchMaxNS - kBatchR) * 32 + 3) & ~3;
@@ -66,7 +67,8 @@ struct BatchArgs {
     unsigned long long *cand_idx;
     unsigned *cand_inst;
     unsigned long long cap;
-    int mix;  // MIN walk: the two-pipe form for instances whose image fits 2^23
+    int mix;  // MIN walk for instances whose image fits 2^23: 0 none (int32),
+              // 1 the two-pipe walk, 2 the deferred-correction walk
 };
 
 
@@ -137,10 +139,33 @@ __global__ void __launch_bounds__(kBatchThreads) batched_walk_kernel(BatchArgs a
                 const int k = a.K[inst * 128 + e];
                 const int kf = __float_as_int((float)k);  // exact when the image fits 2^23
                 sK[e] = k;
-                sKx[e] = make_int4(kf, kf, k, 0);
+                if (a.mix == 1)
+                    sKx[e] = make_int4(kf, kf, k, 0);
             }
-            // two-pipe walk: every partial sum must be exact in FP32, and the
-            // lane needs R walked bits below its three group bits
+            if (a.mix == 2) {
+                // C[pi][u] = K[pi][1] + ... + K[pi][u] (K[pi][0] = 0): a warp
+                // scan over u = lane and u = 32 + lane for each parity
+                float *sCd = reinterpret_cast<float *>(sKx);
+#pragma unroll
+                for (int pi = 0; pi < 2; ++pi) {
+                    int c0 = a.K[inst * 128 + pi * 64 + lane];
+                    int c1 = a.K[inst * 128 + pi * 64 + 32 + lane];
+#pragma unroll
+                    for (int o = 1; o < 32; o <<= 1) {
+                        const int t0 = __shfl_up_sync(0xffffffffu, c0, o);
+                        const int t1 = __shfl_up_sync(0xffffffffu, c1, o);
+                        if (lane >= o) {
+                            c0 += t0;
+                            c1 += t1;
+                        }
+                    }
+                    c1 += __shfl_sync(0xffffffffu, c0, 31);
+                    sCd[pi * 64 + lane] = (float)c0;  // exact: |C| < 2^23
+                    sCd[pi * 64 + 32 + lane] = (float)c1;
+                }
+            }
+            // eight-prefix walks: every partial sum must be exact in FP32, and
+            // the lane needs R walked bits below its three group bits
             use_mix = (MODE == kModeMin) && a.mix && ok && ns >= kBatchR + 3 &&
                       plan->vhat <= (long long)kF32Vmax;
             if (MODE == kModeEmit && ok) {
@@ -158,7 +183,12 @@ __global__ void __launch_bounds__(kBatchThreads) batched_walk_kernel(BatchArgs a
         const unsigned long long p = active ? pl : 0;
         if constexpr (MODE == kModeMin) {
             int m;
-            if (use_mix) {
+            if (use_mix && a.mix == 2) {
+                dfr::Lane<kBatchR> L;
+                dfr::setup<kBatchR>(L, p, n, ns, sS, sLin, sC, 32, lane);
+                m = dfr::walk_min_rt<kBatchR>(L, n, ns, rec4, sC, sS, 32, lane,
+                                              reinterpret_cast<const float *>(sKx));
+            } else if (use_mix) {
                 mix::Lane<kBatchR> L;
                 mix::setup<kBatchR>(L, p, n, ns, sS, sLin, sC, 32, lane);
                 m = mix::walk_min_rt<kBatchR>(L, n, ns, rec4, sC, sS, 32, lane, sKx);
@@ -526,8 +556,9 @@ int dtsize(int dt)
 
 }  // namespace
 
-// One batched pass; mix = 1: float instances take the 2^23 image and every
-// instance whose image fits it takes the two-pipe MIN walk.
+// One batched pass; mix = 1 or 2: float instances take the 2^23 image and every
+// instance whose image fits it takes the two-pipe (1) or the
+// deferred-correction (2) MIN walk; mix = 0: the int32 walk throughout.
 int solve_batched_mode(const void *const *Q, const int *n, const int *dtype, int count,
                        const qbf_options *opt_in, double *min_value, uint64_t *argmin,
                        cudaStream_t s, int *kernel_launches, int mix)
@@ -683,22 +714,25 @@ int solve_batched_mode(const void *const *Q, const int *n, const int *dtype, int
     return QBF_OK;
 }
 
-// QBF_VARIANT_AUTO / SPLIT_MIX: the two-pipe pass; AUTO repeats the batch on
-// the int32 walk (2^31 images) if the wider windows of the FP32 images flag
-// more candidates than the buffer holds.  QBF_VARIANT_SPLIT: the int32 pass.
+// QBF_VARIANT_AUTO / SPLIT_DEFER: the deferred-correction pass, SPLIT_MIX: the
+// two-pipe pass; AUTO repeats the batch on the int32 walk (2^31 images) if the
+// wider windows of the FP32 images flag more candidates than the buffer holds.
+// QBF_VARIANT_SPLIT: the int32 pass.
 int solve_batched(const void *const *Q, const int *n, const int *dtype, int count,
                   const qbf_options *opt_in, double *min_value, uint64_t *argmin,
                   cudaStream_t s, int *kernel_launches)
 {
     const int variant = opt_in ? opt_in->variant : QBF_VARIANT_AUTO;
     if (variant != QBF_VARIANT_AUTO && variant != QBF_VARIANT_SPLIT &&
-        variant != QBF_VARIANT_SPLIT_MIX)
-        return record_error(QBF_ENOTIMPL, "qbf_solve_batched runs the int32 or two-pipe walk");
+        variant != QBF_VARIANT_SPLIT_MIX && variant != QBF_VARIANT_SPLIT_DEFER)
+        return record_error(QBF_ENOTIMPL,
+                            "qbf_solve_batched runs the int32, two-pipe or deferred-correction walk");
     if (variant == QBF_VARIANT_SPLIT)
         return solve_batched_mode(Q, n, dtype, count, opt_in, min_value, argmin, s,
                                   kernel_launches, 0);
     const int rc = solve_batched_mode(Q, n, dtype, count, opt_in, min_value, argmin, s,
-                                      kernel_launches, 1);
+                                      kernel_launches,
+                                      variant == QBF_VARIANT_SPLIT_MIX ? 1 : 2);
     if (rc == QBF_EOVERFLOW && variant == QBF_VARIANT_AUTO)
         return solve_batched_mode(Q, n, dtype, count, opt_in, min_value, argmin, s,
                                   kernel_launches, 0);

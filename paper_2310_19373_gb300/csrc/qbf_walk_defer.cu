@@ -30,183 +30,24 @@
 // unchanged.
 #include <climits>
 
-#include "qbf_f32x2.cuh"
 #include "qbf_internal.cuh"
 #include "qbf_kernels.cuh"
-#include "qbf_walk_core.cuh"
+#include "qbf_walk_defer_core.cuh"
 
 namespace qbf {
 
 __constant__ float c_Cd[2][64];  // C[pi][u], C[pi][0] = 0
 __constant__ float c_Ce[2];      // C[pi][2^R - 1]: a whole block's correction
 
-namespace dfr {
+namespace {
 
-using f32x2::u64;
-
-template <int R>
-struct Lane {
-    u64 v[4];      // (b2 b1 b0) = (00x, 01x, 10x, 11x) as (lo, hi) = (b0 = 0, b0 = 1)
-    u64 GF[4][R];  // lane parts of the low-bit fields, per pair
-    float m[2];    // running minima (two chains)
+// sums from the constant bank (one instance per launch)
+struct ConstC {
+    __device__ __forceinline__ float c(int pi, int u) const { return c_Cd[pi][u]; }
+    __device__ __forceinline__ float ce(int pi) const { return c_Ce[pi]; }
 };
 
-__device__ __forceinline__ float min8(const float (&x)[8])
-{
-    const float a = f32x2::min3(x[0], x[1], x[2]);
-    const float b = f32x2::min3(x[3], x[4], x[5]);
-    const float c = f32x2::min3(x[6], x[7], a);
-    return fminf(b, c);
-}
-
-// one block of 2^R - 1 in-block steps of parity PI
-template <int R, int PI>
-__device__ __forceinline__ void block(Lane<R> &L)
-{
-#pragma unroll
-    for (int u = 1; u < (1 << R); ++u) {
-        const int l = ctz_c(u);
-        const int g = u ^ (u >> 1);
-        const int nb = ((g >> l) & 1) ^ ((l == R - 1) ? PI : 0);
-        float x[8];
-#pragma unroll
-        for (int s = 0; s < 4; ++s) {
-            L.v[s] = nb ? f32x2::add(L.v[s], L.GF[s][l]) : f32x2::sub(L.v[s], L.GF[s][l]);
-            f32x2::unpack(L.v[s], x[2 * s], x[2 * s + 1]);
-        }
-        L.m[u & 1] = fminf(L.m[u & 1], min8(x) + c_Cd[PI][u]);
-    }
-}
-
-// Block transition after a block of parity PI: record (ra, rb) = (T, code,
-// W0..W5) as in the two-pipe walk; the values first take the block's
-// correction back (w -> v), then the mid-bit flip.
-template <int R, int PI>
-__device__ __forceinline__ void trans(Lane<R> &L, const int4 ra, const int4 rb, const int *sC,
-                                      const int *sS, int n, int nsw, int stride, int slot)
-{
-    const int rel = ra.y >> 1;
-    const bool plus = ra.y & 1;
-    const int *Si = sS + (R + rel) * n + nsw;
-    const int c = sC[rel * stride + slot];
-    const int cs = plus ? c : -c;
-    const int t0 = plus ? Si[0] : -Si[0];
-    const int t1 = plus ? Si[1] : -Si[1];
-    const int t2 = plus ? Si[2] : -Si[2];
-    const int base = ra.x + cs;
-    const u64 ce = f32x2::splat(c_Ce[PI]);
-    const int d[8] = {base,      base + t0,      base + t1,      base + t1 + t0,
-                      base + t2, base + t2 + t0, base + t1 + t2, base + t0 + t1 + t2};
-    float x[8];
-#pragma unroll
-    for (int s = 0; s < 4; ++s) {
-        L.v[s] = f32x2::add(f32x2::add(L.v[s], ce),
-                            f32x2::pack((float)d[2 * s], (float)d[2 * s + 1]));
-        f32x2::unpack(L.v[s], x[2 * s], x[2 * s + 1]);
-    }
-    L.m[0] = fminf(L.m[0], min8(x));
-    const int W[6] = {ra.z, ra.w, rb.x, rb.y, rb.z, rb.w};
-#pragma unroll
-    for (int i = 0; i < R; ++i) {
-        const u64 w2 = f32x2::splat((float)W[i]);
-#pragma unroll
-        for (int s = 0; s < 4; ++s)
-            L.GF[s][i] = f32x2::add(L.GF[s][i], w2);
-    }
-}
-
-// Lane set-up for prefix p (variables nsg..n-1, nsg = nsw + 3): the eight
-// start values, the low-bit fields of every group and the lane parts of the
-// mid-bit fields (sC[(i - R) * stride + slot]).
-template <int R>
-__device__ __forceinline__ void setup(Lane<R> &L, unsigned long long p, int n, int nsg,
-                                      const int *sS, const int *sLin, int *sC, int stride, int slot)
-{
-    const int nsw = nsg - 3;
-    const int kp = n - nsg;
-    int va = 0;
-    for (int j = 0; j < kp; ++j) {
-        if (!((p >> j) & 1))
-            continue;
-        const int vj = nsg + j;
-        int row = sLin[vj];
-        for (int jj = j + 1; jj < kp; ++jj)
-            if ((p >> jj) & 1)
-                row += sS[vj * n + nsg + jj];
-        va += row;
-    }
-    int gf[3];
-#pragma unroll
-    for (int t = 0; t < 3; ++t) {
-        int f = sLin[nsw + t];
-        for (int j = 0; j < kp; ++j)
-            if ((p >> j) & 1)
-                f += sS[(nsw + t) * n + nsg + j];
-        gf[t] = f;
-    }
-    const int s01 = sS[nsw * n + nsw + 1], s02 = sS[nsw * n + nsw + 2];
-    const int s12 = sS[(nsw + 1) * n + nsw + 2];
-    // v(b) = va + sum_t b_t gf_t + sum_{t<t'} b_t b_t' S_tt'
-    const int v000 = va, v001 = va + gf[0];
-    const int v010 = va + gf[1], v011 = v010 + gf[0] + s01;
-    const int v100 = va + gf[2], v101 = v100 + gf[0] + s02;
-    const int v110 = v010 + gf[2] + s12, v111 = v011 + gf[2] + s02 + s12;
-    L.v[0] = f32x2::pack((float)v000, (float)v001);
-    L.v[1] = f32x2::pack((float)v010, (float)v011);
-    L.v[2] = f32x2::pack((float)v100, (float)v101);
-    L.v[3] = f32x2::pack((float)v110, (float)v111);
-#pragma unroll
-    for (int ii = 0; ii < R; ++ii) {
-        int c = sLin[ii];
-        for (int j = 0; j < kp; ++j)
-            if ((p >> j) & 1)
-                c += sS[ii * n + nsg + j];
-        const int s0 = sS[ii * n + nsw], s1 = sS[ii * n + nsw + 1], s2 = sS[ii * n + nsw + 2];
-        L.GF[0][ii] = f32x2::pack((float)c, (float)(c + s0));
-        L.GF[1][ii] = f32x2::pack((float)(c + s1), (float)(c + s1 + s0));
-        L.GF[2][ii] = f32x2::pack((float)(c + s2), (float)(c + s2 + s0));
-        L.GF[3][ii] = f32x2::pack((float)(c + s1 + s2), (float)(c + s0 + s1 + s2));
-    }
-    for (int ii = R; ii < nsw; ++ii) {
-        int c = 0;
-        for (int j = 0; j < kp; ++j)
-            if ((p >> j) & 1)
-                c += sS[ii * n + nsg + j];
-        sC[(ii - R) * stride + slot] = c;
-    }
-    L.m[0] = fminf(fminf(fminf((float)v000, (float)v001), fminf((float)v010, (float)v011)),
-                   fminf(fminf((float)v100, (float)v101), fminf((float)v110, (float)v111)));
-    L.m[1] = L.m[0];
-}
-
-// the whole walk of one lane; returns the lane's minimum (an exact integer)
-template <int R>
-__device__ __forceinline__ int walk_min(Lane<R> &L, int n, int nsg, const int4 *rec4,
-                                        const int *sC, const int *sS, int stride, int slot)
-{
-    const int nsw = nsg - 3;
-    const int M = nsw - R;
-    const unsigned nblocks = 1u << M;
-    if (M == 0) {
-        block<R, 0>(L);
-    } else {
-        for (unsigned B = 0; B < nblocks; B += 2) {
-            const int4 r1a = __ldg(rec4 + 2 * (B + 1));
-            const int4 r1b = __ldg(rec4 + 2 * (B + 1) + 1);
-            const unsigned B2 = (B + 2 < nblocks) ? B + 2 : B + 1;
-            const int4 r2a = __ldg(rec4 + 2 * B2);
-            const int4 r2b = __ldg(rec4 + 2 * B2 + 1);
-            block<R, 0>(L);
-            trans<R, 0>(L, r1a, r1b, sC, sS, n, nsw, stride, slot);
-            block<R, 1>(L);
-            if (B + 2 < nblocks)
-                trans<R, 1>(L, r2a, r2b, sC, sS, n, nsw, stride, slot);
-        }
-    }
-    return (int)fminf(L.m[0], L.m[1]);
-}
-
-}  // namespace dfr
+}  // namespace
 
 // a.ns is the suffix width of the certification geometry (nsw + 3); the lane
 // walks the nsw bits below the three group bits for all eight groups.
@@ -243,7 +84,7 @@ __global__ void __launch_bounds__(kWalkThreads)
         const unsigned long long p = active ? i : a.p_lo;
         dfr::Lane<R> L;
         dfr::setup<R>(L, p, n, nsg, sS, sLin, sC, stride, slot);
-        const int mi = dfr::walk_min<R>(L, n, nsg, rec4, sC, sS, stride, slot);
+        const int mi = dfr::walk_min<R>(L, n, nsg, rec4, sC, sS, stride, slot, ConstC{});
         if (active)
             a.pmin[p - a.p_lo] = mi;
         int wm = active ? mi : INT_MAX;

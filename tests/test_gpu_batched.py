@@ -116,12 +116,15 @@ def test_batched_tuner_and_repeat():
         assert (first[0][i], first[1][i]) == (float(v), a)
 
 
-def test_batched_two_pipe_matches_int32_pass():
-    """AUTO (the two-pipe MIN walk for instances whose image fits 2^23) and
+@pytest.mark.parametrize("variant", [qb.QBF_VARIANT_AUTO, qb.QBF_VARIANT_SPLIT_DEFER,
+                                     qb.QBF_VARIANT_SPLIT_MIX], ids=["auto", "defer", "mix"])
+def test_batched_eight_prefix_pass_matches_int32_pass(variant):
+    """AUTO and SPLIT_DEFER (the deferred-correction MIN walk for instances
+    whose image fits 2^23), SPLIT_MIX (the two-pipe walk there) and
     QBF_VARIANT_SPLIT (the int32 walk throughout) certify the same answers on
     a mixed batch: FP32/FP64 and integer instances, small n (int32 walk inside
-    the two-pipe pass) and large n, and an integer instance too large for the
-    2^23 image."""
+    the FP32-image pass) and large n, and an integer instance too large for
+    the 2^23 image."""
     rng = np.random.default_rng(77)
     Qs = []
     for i, n in enumerate([12, 16, 19, 22, 24, 26, 27, 25, 23, 20]):
@@ -135,7 +138,7 @@ def test_batched_two_pipe_matches_int32_pass():
     assert np.abs(big.astype(np.int64)).sum() >= 2 ** 23
     Qs.append(big)
     dQs = to_dev(Qs)
-    a = qb.solve_batched(dQs)
+    a = qb.solve_batched(dQs, variant=variant)
     b = qb.solve_batched(dQs, variant=qb.QBF_VARIANT_SPLIT)
     assert a == b
     for Q, v, x in zip(Qs, *a):
@@ -146,7 +149,7 @@ def test_batched_two_pipe_matches_int32_pass():
 def test_batched_auto_falls_back_when_fp32_windows_overflow():
     """The instance of tests/test_gpu_mix.py whose small terms vanish in the
     2^23 image (2^25 states inside the window) overflows the batch's
-    candidate buffer on the two-pipe pass; AUTO repeats the batch on the int32
+    candidate buffer on the FP32-image passes; AUTO repeats the batch on the int32
     pass and still certifies every instance."""
     n = 26
     Q = np.zeros((n, n))
@@ -155,9 +158,10 @@ def test_batched_auto_falls_back_when_fp32_windows_overflow():
         Q[i, i] = -5e-8 * (1.0 + i / 100.0)
     other = np.random.default_rng(3).normal(size=(20, 20)).astype(np.float32)
     dQs = to_dev([other, Q])
-    with pytest.raises(qb.QbfError) as e:
-        qb.solve_batched(dQs, variant=qb.QBF_VARIANT_SPLIT_MIX)
-    assert e.value.status == qb.QBF_EOVERFLOW
+    for v in (qb.QBF_VARIANT_SPLIT_MIX, qb.QBF_VARIANT_SPLIT_DEFER):
+        with pytest.raises(qb.QbfError) as e:
+            qb.solve_batched(dQs, variant=v)
+        assert e.value.status == qb.QBF_EOVERFLOW
     vmin, am = qb.solve_batched(dQs)
     assert (vmin[1], am[1]) == oracle.brute_min(Q)
     assert am[1] == (1 << n) - 1
