@@ -234,6 +234,34 @@ def run_profile_batched(count, variant=0):
     print(json.dumps({"profile_batched": count, "seconds": dt, "states_per_s": states / dt}))
 
 
+def run_profile_logz(count):
+    """log Z forward and backward (3 betas) on the first `count` instances of
+    the log Z workload (n = 28), twice each (a small case for ncu)."""
+    import torch
+
+    import __graft_entry__
+
+    __graft_entry__.build()
+    from paper_2310_19373_gb300 import _binding as qb
+    from paper_2310_19373_gb300 import inputs
+
+    QL = torch.from_numpy(inputs.config_logz(count=count)).cuda()
+    betas = list(inputs.LOGZ_BETAS)
+    sp = torch.cuda.current_stream().cuda_stream
+    grad = torch.empty((count, 28, 28), dtype=torch.float64, device="cuda")
+    for _ in range(2):
+        t0 = time.perf_counter()
+        qb.qbf_logz(QL.data_ptr(), 28, qb.QBF_F32, count, betas, sp)
+        torch.cuda.synchronize()
+        t1 = time.perf_counter()
+        qb.qbf_logz_backward(QL.data_ptr(), 28, qb.QBF_F32, count, betas, None, grad.data_ptr(),
+                             None, sp)
+        torch.cuda.synchronize()
+        t2 = time.perf_counter()
+    print(json.dumps({"profile_logz": count, "forward_seconds": t1 - t0,
+                      "backward_seconds": t2 - t1}))
+
+
 ALU_OPS = ["IADD3", "IMNMX", "3-input integer min", "FADD", "FFMA", "FMNMX", "3-input FMNMX",
            "packed FADD (f32x2)", "IADD3 + IMNMX pair", "FADD + FMNMX pair"]
 
@@ -373,16 +401,18 @@ def run_variants(dev, flush):
 
 def load_traffic(kernel):
     """DRAM bytes per launch of `kernel` from the committed ncu summary, if its
-    source file is unchanged since the counters were taken (else None)."""
+    source files are unchanged since the counters were taken (else None)."""
     import hashlib
 
     path = os.path.join(ROOT, "profiles", "traffic.json")
     try:
         with open(path) as f:
             t = json.load(f)[kernel]
-        src = os.path.join(ROOT, t["source"])
-        h = hashlib.sha256(open(src, "rb").read()).hexdigest()
-        if h != t["source_sha256"]:
+        h = hashlib.sha256()
+        for src in t.get("sources") or [t["source"]]:
+            with open(os.path.join(ROOT, src), "rb") as f:
+                h.update(f.read())
+        if h.hexdigest() != t["source_sha256"]:
             return None
         return t["bytes_per_full_launch"]
     except (OSError, KeyError, ValueError, TypeError):
@@ -405,6 +435,8 @@ def main():
                     help="kernel form of the headline solve (auto: the library's choice)")
     ap.add_argument("--profile-batched", type=int, default=0,
                     help="run two batched solves on this many instances of the batched workload")
+    ap.add_argument("--profile-logz", type=int, default=0,
+                    help="run log Z forward and backward on this many instances of the log Z workload")
     ap.add_argument("--alu-microbench", action="store_true",
                     help="print the ALU throughput table (roofline denominators) and exit")
     args = ap.parse_args()
@@ -425,6 +457,9 @@ def main():
         return
     if args.profile_batched:
         run_profile_batched(args.profile_batched, VARIANTS[args.variant])
+        return
+    if args.profile_logz:
+        run_profile_logz(args.profile_logz)
         return
 
     import numpy as np
