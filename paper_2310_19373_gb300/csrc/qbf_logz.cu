@@ -98,7 +98,7 @@ template <int R, class F, class G>
 __device__ __forceinline__ void walk2(unsigned vh, unsigned (&GLh)[R], unsigned vl,
                                       unsigned (&GLl)[R], int ns, const int4 *rh, const int4 *rl,
                                       const int *sCh, const int *sCl, int stride, int slot,
-                                      const int *Kh, const int *Kl, F &&visit, G &&flush)
+                                      const int2 *K2, F &&visit, G &&flush)
 {
     const int M = ns - R;
     const unsigned nblocks = 1u << M;
@@ -123,8 +123,9 @@ __device__ __forceinline__ void walk2(unsigned vh, unsigned (&GLh)[R], unsigned 
             constexpr int l = ctz_c(u);
             constexpr int g = u ^ (u >> 1);
             const int nb = ((g >> l) & 1) ^ ((l == R - 1) ? pi : 0);
-            vh = vh + (nb ? GLh[l] : 0u - GLh[l]) + (unsigned)Kh[pi * 64 + u];
-            vl = vl + (nb ? GLl[l] : 0u - GLl[l]) + (unsigned)Kl[pi * 64 + u];
+            const int2 k = K2[pi * 64 + u];  // both limbs' corrections, one load
+            vh = vh + (nb ? GLh[l] : 0u - GLh[l]) + (unsigned)k.x;
+            vl = vl + (nb ? GLl[l] : 0u - GLl[l]) + (unsigned)k.y;
             visit(vh, vl, U, pi);
         });
         flush(B);
@@ -142,8 +143,9 @@ __global__ void __launch_bounds__(kLzThreads) logz_walk_kernel(LzArgs a)
     const Plan *ph = a.plans + (size_t)(b * 2 + a.walk) * 2;
     const Plan *pl = ph + 1;
     int *sSh = sm, *sSl = sSh + n * n, *sLh = sSl + n * n, *sLl = sLh + n;
-    int *sKh = sLl + n, *sKl = sKh + 128;
-    int *sCh = sKl + 128, *sCl = sCh + 2 * (ns - R) * kLzThreads;
+    // (2n^2 + 2n ints before it: 8-byte aligned)
+    int2 *sK2 = reinterpret_cast<int2 *>(sLl + n);
+    int *sCh = reinterpret_cast<int *>(sK2 + 128), *sCl = sCh + 2 * (ns - R) * kLzThreads;
     for (int e = threadIdx.x; e < n * n; e += blockDim.x) {
         sSh[e] = ph->S[e];
         sSl[e] = pl->S[e];
@@ -154,8 +156,7 @@ __global__ void __launch_bounds__(kLzThreads) logz_walk_kernel(LzArgs a)
     }
     const int pidx = (b * 2 + a.walk) * 2;
     for (int e = threadIdx.x; e < 128; e += blockDim.x) {
-        sKh[e] = a.K[pidx * 128 + e];
-        sKl[e] = a.K[(pidx + 1) * 128 + e];
+        sK2[e] = make_int2(a.K[pidx * 128 + e], a.K[(pidx + 1) * 128 + e]);
     }
     __syncthreads();
     if (ph->status != QBF_OK)
@@ -164,10 +165,14 @@ __global__ void __launch_bounds__(kLzThreads) logz_walk_kernel(LzArgs a)
     const bool active = p < a.lanes;
     const unsigned long long pp = active ? p : 0;
     unsigned GLh[R], GLl[R];
-    const unsigned vh = lane_setup<R>(pp, n, ns, sSh, sLh, sCh, kLzThreads, threadIdx.x, GLh);
-    const unsigned vl = lane_setup<R>(pp, n, ns, sSl, sLl, sCl, kLzThreads, threadIdx.x, GLl);
+    // the limbs are walked relative to the argmin's image (the walk is linear
+    // in its start value), so a state's offset to m needs no subtraction
     const unsigned mh = (unsigned)a.shift[(b * 2 + a.walk) * 2];
     const unsigned ml = (unsigned)a.shift[(b * 2 + a.walk) * 2 + 1];
+    const unsigned vh =
+        lane_setup<R>(pp, n, ns, sSh, sLh, sCh, kLzThreads, threadIdx.x, GLh) - mh;
+    const unsigned vl =
+        lane_setup<R>(pp, n, ns, sSl, sLl, sCl, kLzThreads, threadIdx.x, GLl) - ml;
     const int4 *rh = reinterpret_cast<const int4 *>(a.recs + (size_t)pidx * a.rec_stride);
     const int4 *rl = reinterpret_cast<const int4 *>(a.recs + (size_t)(pidx + 1) * a.rec_stride);
 
@@ -182,9 +187,9 @@ __global__ void __launch_bounds__(kLzThreads) logz_walk_kernel(LzArgs a)
             ch[j] = a.ch[j];
             cl[j] = a.cl[j];
         }
-        walk2<R>(vh, GLh, vl, GLl, ns, rh, rl, sCh, sCl, kLzThreads, threadIdx.x, sKh, sKl,
+        walk2<R>(vh, GLh, vl, GLl, ns, rh, rl, sCh, sCl, kLzThreads, threadIdx.x, sK2,
                  [&](unsigned xh, unsigned xl, auto, int) {
-                     const float dh = (float)(int)(xh - mh), dl = (float)(int)(xl - ml);
+                     const float dh = (float)(int)xh, dl = (float)(int)xl;
 #pragma unroll
                      for (int j = 0; j < NB; ++j)
                          if (exact_nb || j < a.nbeta)
@@ -219,11 +224,11 @@ __global__ void __launch_bounds__(kLzThreads) logz_walk_kernel(LzArgs a)
         for (int j = 0; j < (R > 1 ? R - 1 : 1); ++j)
             accLo[j] = 0.f;
         const float ch = a.ch[0], cl = a.cl[0];
-        walk2<R>(vh, GLh, vl, GLl, ns, rh, rl, sCh, sCl, kLzThreads, threadIdx.x, sKh, sKl,
+        walk2<R>(vh, GLh, vl, GLl, ns, rh, rl, sCh, sCl, kLzThreads, threadIdx.x, sK2,
                  [&](unsigned xh, unsigned xl, auto U, int pi) {
                      constexpr int u = decltype(U)::value;
                      constexpr int g = u ^ (u >> 1);
-                     const float dh = (float)(int)(xh - mh), dl = (float)(int)(xl - ml);
+                     const float dh = (float)(int)xh, dl = (float)(int)xl;
                      const float w = ex2_approx(fmaf(dh, ch, dl * cl));
                      acc0 += w;
                      static_for<0, R - 1>([&](auto J) {
