@@ -96,7 +96,11 @@ typedef struct {
     int top_k;          /* number of best states to return, 1..64 (0 -> 1)  */
     int variant;        /* QBF_VARIANT_*                                     */
     int prefix_bits;    /* bits fixed per GPU thread (Section 3.1's m);
-                           -1 = chosen by the planner                        */
+                           -1 = chosen by the planner.  A thread walks at
+                           most 2^20 blocks of 2^6 states: n - prefix_bits
+                           <= 26 (29 for SPLIT_MIX / SPLIT_DEFER, whose
+                           three group bits are not walked), else
+                           QBF_EINVAL                                        */
     int fix_bits;       /* restrict the search to states whose top fix_bits
                            variables x_{n-fix_bits..n-1} equal fix_value;
                            0 = whole space                                   */

@@ -159,6 +159,9 @@ int auto_suffix_bits(int n)
     return ns;
 }
 
+// walked blocks per thread (each 2^R states) are at most 2^kMaxBlockBits
+constexpr int kMaxBlockBits = 20;
+
 struct Geo {
     int n, k, ns, R, M, q;
     int ns_tab;  // suffix width the walk tables are built for
@@ -251,6 +254,12 @@ int plan_geometry(int n, const qbf_options &o, Geo *g)
         g->q = std::min(g->M, 10);
         g->ns_tab = g->ns;
     }
+    // 2^M block records (32 B each) are built per solve and every thread walks
+    // 2^(ns - k') states: bound both before anything is sized from M
+    if (g->M > kMaxBlockBits)
+        return set_err(QBF_EINVAL,
+                       "prefix_bits too small: at most 2^20 blocks of 2^6 states per thread "
+                       "(about 26 suffix bits; use more prefix bits)");
     if (o.fix_bits > 0) {
         g->p_lo = o.fix_value << (k - o.fix_bits);
         g->p_hi = (o.fix_value + 1) << (k - o.fix_bits);

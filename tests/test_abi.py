@@ -73,3 +73,19 @@ def test_constants_match_header():
         m = re.search(rf"\b{name}\s*=\s*(\d+)", text)
         assert m, name
         assert getattr(_binding, name) == int(m.group(1)), name
+
+
+@pytest.mark.parametrize("variant", ["AUTO", "SPLIT", "SPLIT_F32", "SPLIT_MIX", "SPLIT_DEFER",
+                                     "NAIVE"])
+def test_planner_rejects_more_than_2_20_blocks_per_thread(lib, variant):
+    """prefix_bits = 0 at n = 40 would give every thread 2^34 blocks of 2^6
+    states (and size the block records from that count); the planner refuses
+    it before any device memory is touched, so a dummy Q pointer is enough."""
+    from paper_2310_19373_gb300 import _binding as qb
+
+    v = getattr(qb, "QBF_VARIANT_" + variant)
+    opt = qb.make_options(1, v, 0, 0, 0, False)
+    with pytest.raises(qb.QbfError) as e:
+        qb.qbf_solve(256, 40, qb.QBF_F32, opt, None)
+    assert e.value.status == qb.QBF_EINVAL
+    assert "prefix_bits too small" in str(e.value)

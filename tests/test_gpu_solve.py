@@ -253,6 +253,21 @@ def test_errors():
     check_against_oracle(inputs.uniform_int(10, seed=1), top_k=2)
 
 
+@pytest.mark.parametrize("variant,n_ok", [(qb.QBF_VARIANT_SPLIT, 26), (qb.QBF_VARIANT_SPLIT_DEFER, 29)])
+def test_block_count_limit(variant, n_ok):
+    """At most 2^20 blocks of 2^6 states per thread: with prefix_bits = 0 the
+    whole space is one thread's walk, allowed up to 26 suffix bits (29 for the
+    eight-prefix walks, whose three group bits are not walked) and refused
+    one bit beyond."""
+    rng = np.random.default_rng(n_ok)
+    Q = rng.normal(size=(n_ok + 1, n_ok + 1)).astype(np.float32)
+    sol = qb.solve(dev(Q[:n_ok, :n_ok].copy()), prefix_bits=0, variant=variant)
+    assert (sol.min_value, sol.argmin) == oracle.brute_min(Q[:n_ok, :n_ok])
+    with pytest.raises(qb.QbfError) as e:
+        qb.solve(dev(Q), prefix_bits=0, variant=variant)
+    assert e.value.status == qb.QBF_EINVAL
+
+
 def test_host_pointer_path_matches_device_path():
     Q = inputs.config_n20_f64(0)
     a = qb.solve(dev(Q), top_k=8)
