@@ -56,7 +56,8 @@ struct LzArgs {
     unsigned rec_stride;
     const int *K;
     const int *shift;           // per instance and walk: (hi, lo) value of the argmin
-    float ch[kLzMaxBeta], cl[kLzMaxBeta];
+    const float2 *cc;           // [b][kLzMaxBeta]: (c_hi, c_lo) of each beta
+    int beta0;                  // first beta of this launch
     double *laneZ;              // MODE Z:  [b][lane][beta]
     double *laneM1;             // MODE M1: [b][lane][ns]
 };
@@ -184,8 +185,9 @@ __global__ void __launch_bounds__(kLzThreads) logz_walk_kernel(LzArgs a)
 #pragma unroll
         for (int j = 0; j < NB; ++j) {
             acc[j] = sum[j] = comp[j] = 0.f;
-            ch[j] = a.ch[j];
-            cl[j] = a.cl[j];
+            const float2 c2 = a.cc[(size_t)b * kLzMaxBeta + a.beta0 + j];
+            ch[j] = c2.x;
+            cl[j] = c2.y;
         }
         walk2<R>(vh, GLh, vl, GLl, ns, rh, rl, sCh, sCl, kLzThreads, threadIdx.x, sK2,
                  [&](unsigned xh, unsigned xl, auto, int) {
@@ -223,7 +225,8 @@ __global__ void __launch_bounds__(kLzThreads) logz_walk_kernel(LzArgs a)
 #pragma unroll
         for (int j = 0; j < (R > 1 ? R - 1 : 1); ++j)
             accLo[j] = 0.f;
-        const float ch = a.ch[0], cl = a.cl[0];
+        const float2 c2 = a.cc[(size_t)b * kLzMaxBeta + a.beta0];
+        const float ch = c2.x, cl = c2.y;
         walk2<R>(vh, GLh, vl, GLl, ns, rh, rl, sCh, sCl, kLzThreads, threadIdx.x, sK2,
                  [&](unsigned xh, unsigned xl, auto U, int pi) {
                      constexpr int u = decltype(U)::value;
@@ -262,6 +265,27 @@ __global__ void __launch_bounds__(kLzThreads) logz_walk_kernel(LzArgs a)
                 if (j < ns)
                     a.laneM1[((size_t)b * a.lanes + p) * ns + j] = (double)sum[j] - (double)comp[j];
         }
+    }
+}
+
+// Per instance b and beta j < nbeta: c = -beta log2(e) 2^-sigma_b for the hi
+// limb and c 2^-16 for the lo limb, rounded from FP64 (entries j >= nbeta are
+// zero); st[b] = the instance's prepare status.
+__global__ void logz_consts_kernel(const Plan *plans, const double *beta, int nbeta, int batch,
+                                   float2 *cc, int *st)
+{
+    const int b = blockIdx.x * blockDim.x + threadIdx.x;
+    if (b >= batch)
+        return;
+    const Plan *P = plans + (size_t)b * 4;
+    st[b] = P->status;
+    for (int j = 0; j < kLzMaxBeta; ++j) {
+        float2 v = make_float2(0.f, 0.f);
+        if (j < nbeta) {
+            const double c = -beta[j] * 1.4426950408889634 * ldexp(1.0, -P->sigma);
+            v = make_float2((float)c, (float)(c * ldexp(1.0, -16)));
+        }
+        cc[(size_t)b * kLzMaxBeta + j] = v;
     }
 }
 
@@ -478,7 +502,7 @@ LzGeo lz_geo(int n)
 }
 
 struct LzLayout {
-    size_t plans, recs, K, shift, argmin, laneZA, laneM1, laneZB, beta, total;
+    size_t plans, recs, K, shift, argmin, laneZA, laneM1, laneZB, beta, cc, st, total;
 };
 
 LzLayout lz_layout(const LzGeo &g, int batch, int nbeta)
@@ -499,6 +523,8 @@ LzLayout lz_layout(const LzGeo &g, int batch, int nbeta)
     L.laneM1 = take(sizeof(double) * g.lanesA * batch * g.nsA);
     L.laneZB = take(sizeof(double) * g.lanesB * batch * std::max(nbeta, 1));
     L.beta = take(sizeof(double) * kLzMaxBeta);
+    L.cc = take(sizeof(float2) * kLzMaxBeta * batch);
+    L.st = take(sizeof(int) * batch);
     L.total = o;
     return L;
 }
@@ -631,29 +657,30 @@ LzArgs lz_args(const LzGeo &g, char *base, const LzLayout &L, int walk, int nbet
     a.shift = (const int *)(base + L.shift);
     a.laneZ = (double *)(base + (walk ? L.laneZB : L.laneZA));
     a.laneM1 = (double *)(base + L.laneM1);
+    a.cc = (const float2 *)(base + L.cc);
+    a.beta0 = 0;
     (void)beta;
     return a;
 }
 
-// c = -beta log2(e) 2^-sigma (hi limb) and 2^-(sigma+16) (lo limb); sigma is
-// per instance but the same for every instance of a batch only by chance, so
-// the kernels get sigma through the plans: the host reads it back first.
-int lz_sigmas(const Plan *plans_dev, int batch, std::vector<int> &sig, cudaStream_t s)
+// Upload the betas, derive every instance's exp constants on the device and
+// check that every instance prepared (one status download).
+int lz_consts(const LzLayout &L, char *base, int batch, const double *beta, int nbeta,
+              cudaStream_t s)
 {
-    sig.assign(batch, 0);
-    for (int b = 0; b < batch; ++b) {
-        L_CUDA(cudaMemcpyAsync(&sig[b], &plans_dev[(size_t)b * 4].sigma, sizeof(int),
-                               cudaMemcpyDeviceToHost, s),
-               "sigma");
-    }
+    L_CUDA(cudaMemcpyAsync(base + L.beta, beta, sizeof(double) * nbeta, cudaMemcpyHostToDevice, s),
+           "beta upload");
+    logz_consts_kernel<<<(batch + 127) / 128, 128, 0, s>>>(
+        (const Plan *)(base + L.plans), (const double *)(base + L.beta), nbeta, batch,
+        (float2 *)(base + L.cc), (int *)(base + L.st));
+    L_CUDA(cudaGetLastError(), "log Z constants");
+    std::vector<int> st(batch);
+    L_CUDA(cudaMemcpyAsync(st.data(), base + L.st, sizeof(int) * batch, cudaMemcpyDeviceToHost, s),
+           "status");
     L_CUDA(cudaStreamSynchronize(s), "log Z set-up");
-    for (int b = 0; b < batch; ++b) {
-        int st = 0;
-        L_CUDA(cudaMemcpy(&st, &plans_dev[(size_t)b * 4].status, sizeof(int), cudaMemcpyDeviceToHost),
-               "status");
-        if (st != QBF_OK)
-            return record_error(st, ("instance " + std::to_string(b) + ": prepare failed").c_str());
-    }
+    for (int b = 0; b < batch; ++b)
+        if (st[b] != QBF_OK)
+            return record_error(st[b], ("instance " + std::to_string(b) + ": prepare failed").c_str());
     return QBF_OK;
 }
 
@@ -675,38 +702,12 @@ int logz_forward(const void *Q, int n, int dtype, int batch, const double *beta,
         return rc;
     if ((rc = lz_setup(Q, n, dtype, batch, g, base, L, min_value, argmin, s)))
         return rc;
-    std::vector<int> sig;
-    if ((rc = lz_sigmas((const Plan *)(base + L.plans), batch, sig, s)))
+    if ((rc = lz_consts(L, base, batch, beta, nbeta, s)))
         return rc;
-    // one walk-A launch per distinct sigma (normally one for the whole batch)
-    std::vector<double> Zl;
-    L_CUDA(cudaMemcpyAsync(base + L.beta, beta, sizeof(double) * nbeta, cudaMemcpyHostToDevice, s),
-           "beta upload");
-    std::vector<int> done(batch, 0);
-    for (int b0 = 0; b0 < batch; ++b0) {
-        if (done[b0])
-            continue;
-        // instances sharing sigma b0's value are walked together only if they
-        // form a contiguous run; otherwise walk instance by instance
-        int b1 = b0;
-        while (b1 + 1 < batch && sig[b1 + 1] == sig[b0])
-            ++b1;
-        LzArgs a = lz_args(g, base, L, 0, nbeta, beta, 0);
-        for (int j = 0; j < nbeta; ++j) {
-            const double c = -beta[j] * 1.4426950408889634 * ldexp(1.0, -sig[b0]);
-            a.ch[j] = (float)c;
-            a.cl[j] = (float)(c * ldexp(1.0, -16));
-        }
-        // offset the instance range by adjusting the base pointers
-        a.plans += (size_t)b0 * 4;
-        a.K += (size_t)b0 * 4 * 128;
-        a.recs += (size_t)b0 * 4 * g.rec_stride;
-        a.shift += (size_t)b0 * 4;
-        a.laneZ += (size_t)b0 * g.lanesA * nbeta;
-        L_CUDA(launch_lz<kModeZ>(a.R, a, b1 - b0 + 1, s), "log Z walk");
-        for (int b = b0; b <= b1; ++b)
-            done[b] = 1;
-    }
+    // walk A over every instance in one launch (each instance reads its own
+    // scale-dependent constants)
+    LzArgs a = lz_args(g, base, L, 0, nbeta, beta, 0);
+    L_CUDA(launch_lz<kModeZ>(a.R, a, batch, s), "log Z walk");
     double *dlogz = (double *)(base + L.laneM1);  // reuse: batch * nbeta doubles
     logz_reduce_kernel<<<batch, 256, 0, s>>>((const Plan *)(base + L.plans),
                                              (const double *)(base + L.laneZA), g.lanesA, nbeta,
@@ -737,47 +738,18 @@ int logz_backward(const void *Q, int n, int dtype, int batch, const double *beta
     std::vector<uint64_t> am(batch);
     if ((rc = lz_setup(Q, n, dtype, batch, g, base, L, vmin.data(), am.data(), s)))
         return rc;
-    std::vector<int> sig;
-    if ((rc = lz_sigmas((const Plan *)(base + L.plans), batch, sig, s)))
+    if ((rc = lz_consts(L, base, batch, beta, nbeta, s)))
         return rc;
     L_CUDA(cudaMemsetAsync(grad, 0, sizeof(double) * batch * n * n, s), "grad clear");
     // walk B (rotated variables) needs only Z: one pass for every beta
-    for (int b = 0; b < batch;) {
-        int b1 = b;
-        while (b1 + 1 < batch && sig[b1 + 1] == sig[b])
-            ++b1;
+    {
         LzArgs a = lz_args(g, base, L, 1, nbeta, beta, 0);
-        for (int j = 0; j < nbeta; ++j) {
-            const double c = -beta[j] * 1.4426950408889634 * ldexp(1.0, -sig[b]);
-            a.ch[j] = (float)c;
-            a.cl[j] = (float)(c * ldexp(1.0, -16));
-        }
-        a.plans += (size_t)b * 4;
-        a.K += (size_t)b * 4 * 128;
-        a.recs += (size_t)b * 4 * g.rec_stride;
-        a.shift += (size_t)b * 4;
-        a.laneZ += (size_t)b * a.lanes * nbeta;
-        L_CUDA(launch_lz<kModeZ>(a.R, a, b1 - b + 1, s), "log Z walk (rotated)");
-        b = b1 + 1;
+        L_CUDA(launch_lz<kModeZ>(a.R, a, batch, s), "log Z walk (rotated)");
     }
     for (int j = 0; j < nbeta; ++j) {
-        for (int b = 0; b < batch;) {
-            int b1 = b;
-            while (b1 + 1 < batch && sig[b1 + 1] == sig[b])
-                ++b1;
-            const double c = -beta[j] * 1.4426950408889634 * ldexp(1.0, -sig[b]);
-            LzArgs a = lz_args(g, base, L, 0, 1, beta, 0);
-            a.ch[0] = (float)c;
-            a.cl[0] = (float)(c * ldexp(1.0, -16));
-            a.plans += (size_t)b * 4;
-            a.K += (size_t)b * 4 * 128;
-            a.recs += (size_t)b * 4 * g.rec_stride;
-            a.shift += (size_t)b * 4;
-            a.laneZ += (size_t)b * a.lanes;
-            a.laneM1 += (size_t)b * a.lanes * g.nsA;
-            L_CUDA(launch_lz<kModeM1>(a.R, a, b1 - b + 1, s), "log Z moment walk");
-            b = b1 + 1;
-        }
+        LzArgs a = lz_args(g, base, L, 0, 1, beta, 0);
+        a.beta0 = j;
+        L_CUDA(launch_lz<kModeM1>(a.R, a, batch, s), "log Z moment walk");
         logz_moments_kernel<<<batch * n, 256, 0, s>>>(
             n, g.nsA, g.lanesA, g.lanesB, (const double *)(base + L.laneZA),
             (const double *)(base + L.laneM1), (const double *)(base + L.laneZB), nbeta, j,
