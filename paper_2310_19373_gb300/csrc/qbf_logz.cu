@@ -414,33 +414,35 @@ __global__ void __launch_bounds__(256) logz_moments_kernel(
     const double ZAt = block_sum_fixed(za, lanesA, 1, red);
     const double ZBt = block_sum_fixed(zb, lanesB, zb_stride, red);
     const double u = up ? up[b * up_stride + up_off] : 1.0;
-#pragma unroll 1
-    for (int j = i; j < n; ++j) {
-        double v = 0.0;
+    // every column j at once: a fixed-order shuffle sum per warp, then the
+    // warps' partial sums in warp order (deterministic)
+    __shared__ double part[256 / 32][QBF_BATCH_MAX_N];
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
 #pragma unroll
-        for (int jj = 0; jj < QBF_BATCH_MAX_N; ++jj)
-            if (jj == j)
-                v = acc[jj];
-        red[threadIdx.x] = v;
-        __syncthreads();
-        for (int o = blockDim.x / 2; o > 0; o >>= 1) {
-            if (threadIdx.x < o)
-                red[threadIdx.x] += red[threadIdx.x + o];
-            __syncthreads();
+    for (int j = 0; j < QBF_BATCH_MAX_N; ++j) {
+        double v = acc[j];
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1)
+            v += __shfl_down_sync(0xffffffffu, v, o);
+        if (lane == 0)
+            part[wid][j] = v;
+    }
+    __syncthreads();
+    const int j = threadIdx.x;
+    if (j >= i && j < n) {
+        double sum = 0.0;
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w)
+            sum += part[w][j];
+        const double E = sum / ((i < nsA && j < nsA) ? ZBt : ZAt);
+        const double gval = u * (-beta) * E;
+        grad[(size_t)b * n * n + i * n + j] += gval;
+        if (i != j)
+            grad[(size_t)b * n * n + j * n + i] += gval;
+        if (moment) {
+            double *mm = moment + (size_t)b * moment_stride + moment_off;
+            mm[i * n + j] = E;
+            mm[j * n + i] = E;
         }
-        if (threadIdx.x == 0) {
-            const double E = red[0] / ((i < nsA && j < nsA) ? ZBt : ZAt);
-            const double gval = u * (-beta) * E;
-            grad[(size_t)b * n * n + i * n + j] += gval;
-            if (i != j)
-                grad[(size_t)b * n * n + j * n + i] += gval;
-            if (moment) {
-                double *mm = moment + (size_t)b * moment_stride + moment_off;
-                mm[i * n + j] = E;
-                mm[j * n + i] = E;
-            }
-        }
-        __syncthreads();
     }
 }
 
