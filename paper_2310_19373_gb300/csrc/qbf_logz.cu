@@ -217,6 +217,7 @@ __global__ void __launch_bounds__(kLzThreads) logz_walk_kernel(LzArgs a)
         // block parity, bits >= R are constant over a block: they take the
         // block total at the flush.
         float acc0 = 0.f, sum0 = 0.f, comp0 = 0.f, accTop = 0.f;
+        float wq[4] = {0.f, 0.f, 0.f, 0.f};  // the current quad's weights (R >= 3)
         float accLo[R > 1 ? R - 1 : 1];
         float sum[kLzMaxNs], comp[kLzMaxNs];
 #pragma unroll
@@ -233,13 +234,35 @@ __global__ void __launch_bounds__(kLzThreads) logz_walk_kernel(LzArgs a)
                      constexpr int g = u ^ (u >> 1);
                      const float dh = (float)(int)xh, dl = (float)(int)xl;
                      const float w = ex2_approx(fmaf(dh, ch, dl * cl));
-                     acc0 += w;
-                     static_for<0, R - 1>([&](auto J) {
-                         if constexpr ((g >> decltype(J)::value) & 1)
-                             accLo[decltype(J)::value] += w;
-                     });
-                     if (((g >> (R - 1)) & 1) ^ pi)
-                         accTop += w;
+                     if constexpr (R >= 3) {
+                         // aligned quads of steps: bits 2.. of the Gray code are
+                         // constant over a quad, bit 0 is set at its steps 1
+                         // and 2, bit 1 at steps 0, 1 or 2, 3 (by bit 2 of u);
+                         // sum the quad first, then add it once per set bit
+                         wq[u & 3] = w;
+                         if constexpr ((u & 3) == 3) {
+                             const float p01 = wq[0] + wq[1], p23 = wq[2] + wq[3];
+                             const float q = p01 + p23;
+                             acc0 += q;
+                             accLo[0] += wq[1] + wq[2];
+                             if constexpr (R - 1 > 1)
+                                 accLo[1] += ((u >> 2) & 1) ? p01 : p23;
+                             static_for<2, R - 1>([&](auto J) {
+                                 if constexpr ((g >> decltype(J)::value) & 1)
+                                     accLo[decltype(J)::value] += q;
+                             });
+                             if (((g >> (R - 1)) & 1) ^ pi)
+                                 accTop += q;
+                         }
+                     } else {
+                         acc0 += w;
+                         static_for<0, R - 1>([&](auto J) {
+                             if constexpr ((g >> decltype(J)::value) & 1)
+                                 accLo[decltype(J)::value] += w;
+                         });
+                         if (((g >> (R - 1)) & 1) ^ pi)
+                             accTop += w;
+                     }
                  },
                  [&](unsigned B) {
                      const float blk = acc0;
