@@ -45,10 +45,10 @@ namespace {
 
 constexpr int kLzThreads = 128;
 constexpr int kLzMaxBeta = 8;
-constexpr int kLzMaxNs = 17;
 
 struct LzArgs {
     int n, ns, kp, nbeta, R;
+    int batch;                  // instances in this launch
     unsigned long long lanes;   // 2^kp prefixes per instance
     const Plan *plans;          // (b * 2 + w) * 2 + limb
     int walk;                   // 0: A, 1: B
@@ -63,7 +63,8 @@ struct LzArgs {
 };
 
 constexpr int kModeZ = 0;   // Z for every beta
-constexpr int kModeM1 = 1;  // Z and M1 for one beta
+constexpr int kModeM1 = 1;  // Z and M1 for up to kLzM1Beta betas
+constexpr int kLzM1Beta = 3;
 
 __device__ __forceinline__ float ex2_approx(float x)
 {
@@ -212,81 +213,114 @@ __global__ void __launch_bounds__(kLzThreads) logz_walk_kernel(LzArgs a)
                         (double)sum[j] - (double)comp[j];
         }
     } else {
-        // Z and M1[j] = sum of w over the states with suffix bit j set.  Bits
-        // below R - 1 are compile-time per step, bit R - 1 depends on the
-        // block parity, bits >= R are constant over a block: they take the
-        // block total at the flush.
-        float acc0 = 0.f, sum0 = 0.f, comp0 = 0.f, accTop = 0.f;
-        float wq[4] = {0.f, 0.f, 0.f, 0.f};  // the current quad's weights (R >= 3)
-        float accLo[R > 1 ? R - 1 : 1];
-        float sum[kLzMaxNs], comp[kLzMaxNs];
+        // For each of the NB betas of this launch: Z and M1[j] = sum of w
+        // over the states with suffix bit j set.  Bits below R - 1 are
+        // compile-time per step, bit R - 1 depends on the block parity, bits
+        // >= R are constant over a block: they take the block total at the
+        // flush.  Z and the low R bits keep Kahan sums in registers, the mid
+        // bits in this thread's column of shared memory (sMid).
+        float acc0[NB], accTop[NB], accLo[NB][R > 1 ? R - 1 : 1], wq[NB][4];
+        float sum0[NB], comp0[NB], sumLo[NB][R], compLo[NB][R], ch[NB], cl[NB];
+        float *sMid = reinterpret_cast<float *>(sCl + 2 * (ns - R) * kLzThreads);
+        const int nmid = ns - R;
 #pragma unroll
-        for (int j = 0; j < kLzMaxNs; ++j)
-            sum[j] = comp[j] = 0.f;
+        for (int bb = 0; bb < NB; ++bb) {
+            const float2 c2 = a.cc[(size_t)b * kLzMaxBeta + a.beta0 + bb];
+            ch[bb] = c2.x;
+            cl[bb] = c2.y;
+            acc0[bb] = accTop[bb] = sum0[bb] = comp0[bb] = 0.f;
 #pragma unroll
-        for (int j = 0; j < (R > 1 ? R - 1 : 1); ++j)
-            accLo[j] = 0.f;
-        const float2 c2 = a.cc[(size_t)b * kLzMaxBeta + a.beta0];
-        const float ch = c2.x, cl = c2.y;
+            for (int q = 0; q < 4; ++q)
+                wq[bb][q] = 0.f;
+#pragma unroll
+            for (int J = 0; J < (R > 1 ? R - 1 : 1); ++J)
+                accLo[bb][J] = 0.f;
+#pragma unroll
+            for (int J = 0; J < R; ++J)
+                sumLo[bb][J] = compLo[bb][J] = 0.f;
+        }
+        for (int e = 0; e < 2 * NB * nmid; ++e)
+            sMid[e * kLzThreads + threadIdx.x] = 0.f;
         walk2<R>(vh, GLh, vl, GLl, ns, rh, rl, sCh, sCl, kLzThreads, threadIdx.x, sK2,
                  [&](unsigned xh, unsigned xl, auto U, int pi) {
                      constexpr int u = decltype(U)::value;
                      constexpr int g = u ^ (u >> 1);
                      const float dh = (float)(int)xh, dl = (float)(int)xl;
-                     const float w = ex2_approx(fmaf(dh, ch, dl * cl));
-                     if constexpr (R >= 3) {
-                         // aligned quads of steps: bits 2.. of the Gray code are
-                         // constant over a quad, bit 0 is set at its steps 1
-                         // and 2, bit 1 at steps 0, 1 or 2, 3 (by bit 2 of u);
-                         // sum the quad first, then add it once per set bit
-                         wq[u & 3] = w;
-                         if constexpr ((u & 3) == 3) {
-                             const float p01 = wq[0] + wq[1], p23 = wq[2] + wq[3];
-                             const float q = p01 + p23;
-                             acc0 += q;
-                             accLo[0] += wq[1] + wq[2];
-                             if constexpr (R - 1 > 1)
-                                 accLo[1] += ((u >> 2) & 1) ? p01 : p23;
-                             static_for<2, R - 1>([&](auto J) {
+#pragma unroll
+                     for (int bb = 0; bb < NB; ++bb) {
+                         const float w = ex2_approx(fmaf(dh, ch[bb], dl * cl[bb]));
+                         if constexpr (R >= 3) {
+                             // aligned quads of steps: bits 2.. of the Gray code
+                             // are constant over a quad, bit 0 is set at its
+                             // steps 1 and 2, bit 1 at steps 0, 1 or 2, 3 (by
+                             // bit 2 of u); sum the quad first, then add it
+                             // once per set bit
+                             wq[bb][u & 3] = w;
+                             if constexpr ((u & 3) == 3) {
+                                 const float p01 = wq[bb][0] + wq[bb][1];
+                                 const float p23 = wq[bb][2] + wq[bb][3];
+                                 const float q = p01 + p23;
+                                 acc0[bb] += q;
+                                 accLo[bb][0] += wq[bb][1] + wq[bb][2];
+                                 accLo[bb][1] += ((u >> 2) & 1) ? p01 : p23;
+                                 static_for<2, R - 1>([&](auto J) {
+                                     if constexpr ((g >> decltype(J)::value) & 1)
+                                         accLo[bb][decltype(J)::value] += q;
+                                 });
+                                 if (((g >> (R - 1)) & 1) ^ pi)
+                                     accTop[bb] += q;
+                             }
+                         } else {
+                             acc0[bb] += w;
+                             static_for<0, R - 1>([&](auto J) {
                                  if constexpr ((g >> decltype(J)::value) & 1)
-                                     accLo[decltype(J)::value] += q;
+                                     accLo[bb][decltype(J)::value] += w;
                              });
                              if (((g >> (R - 1)) & 1) ^ pi)
-                                 accTop += q;
+                                 accTop[bb] += w;
                          }
-                     } else {
-                         acc0 += w;
-                         static_for<0, R - 1>([&](auto J) {
-                             if constexpr ((g >> decltype(J)::value) & 1)
-                                 accLo[decltype(J)::value] += w;
-                         });
-                         if (((g >> (R - 1)) & 1) ^ pi)
-                             accTop += w;
                      }
                  },
                  [&](unsigned B) {
-                     const float blk = acc0;
-                     kahan_add(sum0, comp0, acc0);
-                     acc0 = 0.f;
-#pragma unroll
-                     for (int j = 0; j < R - 1; ++j) {
-                         kahan_add(sum[j], comp[j], accLo[j]);
-                         accLo[j] = 0.f;
-                     }
-                     kahan_add(sum[R - 1], comp[R - 1], accTop);
-                     accTop = 0.f;
                      const unsigned gB = B ^ (B >> 1);
 #pragma unroll
-                     for (int j = R; j < kLzMaxNs; ++j)
-                         if (j < ns && ((gB >> (j - R)) & 1u))
-                             kahan_add(sum[j], comp[j], blk);
+                     for (int bb = 0; bb < NB; ++bb) {
+                         const float blk = acc0[bb];
+                         kahan_add(sum0[bb], comp0[bb], acc0[bb]);
+                         acc0[bb] = 0.f;
+#pragma unroll
+                         for (int J = 0; J < R - 1; ++J) {
+                             kahan_add(sumLo[bb][J], compLo[bb][J], accLo[bb][J]);
+                             accLo[bb][J] = 0.f;
+                         }
+                         kahan_add(sumLo[bb][R - 1], compLo[bb][R - 1], accTop[bb]);
+                         accTop[bb] = 0.f;
+                         for (int j = 0; j < nmid; ++j) {
+                             if (!((gB >> j) & 1u))
+                                 continue;
+                             float *ps = sMid + (size_t)((j * NB + bb) * 2) * kLzThreads + threadIdx.x;
+                             float sv = ps[0], cv = ps[kLzThreads];
+                             kahan_add(sv, cv, blk);
+                             ps[0] = sv;
+                             ps[kLzThreads] = cv;
+                         }
+                     }
                  });
         if (active) {
-            a.laneZ[(size_t)b * a.lanes + p] = (double)sum0 - (double)comp0;
 #pragma unroll
-            for (int j = 0; j < kLzMaxNs; ++j)
-                if (j < ns)
-                    a.laneM1[((size_t)b * a.lanes + p) * ns + j] = (double)sum[j] - (double)comp[j];
+            for (int bb = 0; bb < NB; ++bb) {
+                // beta bb's Z and M1 go to its own slab: [bb][b][lane](...)
+                const size_t slab = (size_t)bb * a.batch * a.lanes;
+                a.laneZ[slab + (size_t)b * a.lanes + p] = (double)sum0[bb] - (double)comp0[bb];
+                double *m1 = a.laneM1 + (slab + (size_t)b * a.lanes + p) * ns;
+#pragma unroll
+                for (int J = 0; J < R; ++J)
+                    m1[J] = (double)sumLo[bb][J] - (double)compLo[bb][J];
+                for (int j = 0; j < nmid; ++j) {
+                    const float *ps = sMid + (size_t)((j * NB + bb) * 2) * kLzThreads + threadIdx.x;
+                    m1[R + j] = (double)ps[0] - (double)ps[kLzThreads];
+                }
+            }
         }
     }
 }
@@ -545,7 +579,7 @@ LzLayout lz_layout(const LzGeo &g, int batch, int nbeta)
     L.shift = take(sizeof(int) * 4 * batch);
     L.argmin = take(sizeof(unsigned long long) * batch);
     L.laneZA = take(sizeof(double) * g.lanesA * batch * std::max(nbeta, 1));
-    L.laneM1 = take(sizeof(double) * g.lanesA * batch * g.nsA);
+    L.laneM1 = take(sizeof(double) * g.lanesA * batch * g.nsA * std::min(nbeta, kLzM1Beta));
     L.laneZB = take(sizeof(double) * g.lanesB * batch * std::max(nbeta, 1));
     L.beta = take(sizeof(double) * kLzMaxBeta);
     L.cc = take(sizeof(float2) * kLzMaxBeta * batch);
@@ -575,10 +609,14 @@ int lz_pool(size_t bytes, char **base)
 }
 
 template <int MODE, int NB>
-cudaError_t launch_lz_nb(int R, const LzArgs &a, int batch, cudaStream_t s)
+cudaError_t launch_lz_nb(int R, const LzArgs &a_in, int batch, cudaStream_t s)
 {
+    LzArgs a = a_in;
+    a.batch = batch;
+    // + the moment walk's mid-bit Kahan sums: 2 floats per beta and mid bit
     const size_t smem =
-        sizeof(int) * (2 * a.n * a.n + 2 * a.n + 256 + 2 * 2 * (a.ns - R) * kLzThreads);
+        sizeof(int) * (2 * a.n * a.n + 2 * a.n + 256 + 2 * 2 * (a.ns - R) * kLzThreads +
+                       (MODE == kModeM1 ? 2 * NB * (a.ns - R) * kLzThreads : 0));
     const unsigned long long bpi = (a.lanes + kLzThreads - 1) / kLzThreads;
     const unsigned grid = (unsigned)(bpi * batch);
     auto go = [&](auto kern) {
@@ -599,12 +637,18 @@ cudaError_t launch_lz_nb(int R, const LzArgs &a, int batch, cudaStream_t s)
     }
 }
 
-// the moment walk takes one beta; the Z walk is compiled per beta count
+// the moment walk takes up to kLzM1Beta betas per launch; the Z walk is
+// compiled per beta count
 template <int MODE>
 cudaError_t launch_lz(int R, const LzArgs &a, int batch, cudaStream_t s)
 {
     if constexpr (MODE == kModeM1) {
-        return launch_lz_nb<MODE, 1>(R, a, batch, s);
+        switch (a.nbeta) {
+        case 1: return launch_lz_nb<MODE, 1>(R, a, batch, s);
+        case 2: return launch_lz_nb<MODE, 2>(R, a, batch, s);
+        case 3: return launch_lz_nb<MODE, 3>(R, a, batch, s);
+        default: return cudaErrorInvalidValue;
+        }
     } else {
         switch (a.nbeta) {
         case 1: return launch_lz_nb<MODE, 1>(R, a, batch, s);
@@ -771,15 +815,23 @@ int logz_backward(const void *Q, int n, int dtype, int batch, const double *beta
         LzArgs a = lz_args(g, base, L, 1, nbeta, beta, 0);
         L_CUDA(launch_lz<kModeZ>(a.R, a, batch, s), "log Z walk (rotated)");
     }
-    for (int j = 0; j < nbeta; ++j) {
-        LzArgs a = lz_args(g, base, L, 0, 1, beta, 0);
-        a.beta0 = j;
+    // walk A with first moments, up to kLzM1Beta betas per launch; beta
+    // j0 + jj leaves its Z and M1 in slab jj of laneZA / laneM1
+    for (int j0 = 0; j0 < nbeta; j0 += kLzM1Beta) {
+        const int nb = std::min(kLzM1Beta, nbeta - j0);
+        LzArgs a = lz_args(g, base, L, 0, nb, beta, 0);
+        a.beta0 = j0;
         L_CUDA(launch_lz<kModeM1>(a.R, a, batch, s), "log Z moment walk");
-        logz_moments_kernel<<<batch * n, 256, 0, s>>>(
-            n, g.nsA, g.lanesA, g.lanesB, (const double *)(base + L.laneZA),
-            (const double *)(base + L.laneM1), (const double *)(base + L.laneZB), nbeta, j,
-            beta[j], upstream, nbeta, j, grad, moment, nbeta * n * n, j * n * n);
-        L_CUDA(cudaGetLastError(), "log Z moments");
+        for (int jj = 0; jj < nb; ++jj) {
+            const int j = j0 + jj;
+            const size_t slab = (size_t)jj * batch * g.lanesA;
+            logz_moments_kernel<<<batch * n, 256, 0, s>>>(
+                n, g.nsA, g.lanesA, g.lanesB, (const double *)(base + L.laneZA) + slab,
+                (const double *)(base + L.laneM1) + slab * g.nsA,
+                (const double *)(base + L.laneZB), nbeta, j, beta[j], upstream, nbeta, j, grad,
+                moment, nbeta * n * n, j * n * n);
+            L_CUDA(cudaGetLastError(), "log Z moments");
+        }
     }
     L_CUDA(cudaStreamSynchronize(s), "log Z backward");
     return QBF_OK;

@@ -49,6 +49,26 @@ def test_logz_forward_and_moments_against_oracle(n):
         assert np.allclose(grad[b], want, rtol=RTOL, atol=1e-9)
 
 
+@pytest.mark.parametrize("betas", [[0.2, 1.0, 3.0, 7.0], [0.05, 0.1, 0.3, 1.0, 2.0, 5.0, 10.0]])
+def test_logz_many_betas_against_oracle(betas):
+    """More betas than one moment walk takes (three): the backward splits
+    them over several launches (3 + 1, 3 + 3 + 1), the forward predicates
+    the Z walk compiled for eight."""
+    n = 11
+    rng = np.random.default_rng(950 + len(betas))
+    Qb = np.triu(rng.normal(0, 1 / np.sqrt(n), size=(2, n, n))).astype(np.float32)
+    lz, vmin, am = run_forward(Qb, betas)
+    grad, mom = run_backward(Qb, betas)
+    for b in range(2):
+        olz, oE, ov, oa = oracle.logz(Qb[b], betas)
+        assert (vmin[b], am[b]) == (ov, oa)
+        for j, beta in enumerate(betas):
+            assert abs(lz[b][j] - olz[j]) <= RTOL * abs(olz[j]) + 1e-9, (b, beta)
+            assert np.max(np.abs(mom[b, j] - oE[j]) - RTOL * np.abs(oE[j])) <= 1e-9, (b, beta)
+        want = sum(-beta * oE[j] for j, beta in enumerate(betas))
+        assert np.allclose(grad[b], want, rtol=RTOL, atol=1e-9)
+
+
 def test_logz_integer_and_f64_inputs():
     rng = np.random.default_rng(4)
     for Qb in (rng.integers(-3, 4, size=(2, 10, 10)).astype(np.int32),
