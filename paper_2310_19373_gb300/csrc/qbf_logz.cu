@@ -10,8 +10,9 @@
 // f at scale 2^(s+16) = hi_value * 2^16 + lo_value, both limbs walked exactly in
 // int32 in lockstep.  The shift m is the image value of the certified argmin
 // (from the batched minimiser), so every weight w = exp(-beta (f - m)) is <= ~1.
-// w = ex2(d_hi * c_hi + d_lo * c_lo) with d the limb differences to m and
-// c = -beta log2(e) 2^-(s or s+16).  Weights are summed in FP32 per block of
+// w = ex2(c (d_hi + d_lo 2^-16)) with d the limb differences to m and
+// c = -beta log2(e) 2^-s (the FP32 argument keeps 24 bits either way: the lo
+// limb matters only where d_hi is small).  Weights are summed in FP32 per block of
 // 2^R states, blocks are added with Kahan compensation per lane, lanes in FP64
 // in a fixed order.
 //
@@ -182,21 +183,22 @@ __global__ void __launch_bounds__(kLzThreads) logz_walk_kernel(LzArgs a)
         // NB betas (exactly a.nbeta for NB <= 4; up to NB = 8 with the rest
         // predicated off), each an FP32 block sum flushed into a Kahan sum
         constexpr bool exact_nb = NB <= 4;
-        float acc[NB], sum[NB], comp[NB], ch[NB], cl[NB];
+        float acc[NB], sum[NB], comp[NB], ch[NB];
 #pragma unroll
         for (int j = 0; j < NB; ++j) {
             acc[j] = sum[j] = comp[j] = 0.f;
             const float2 c2 = a.cc[(size_t)b * kLzMaxBeta + a.beta0 + j];
             ch[j] = c2.x;
-            cl[j] = c2.y;
         }
         walk2<R>(vh, GLh, vl, GLl, ns, rh, rl, sCh, sCl, kLzThreads, threadIdx.x, sK2,
                  [&](unsigned xh, unsigned xl, auto, int) {
-                     const float dh = (float)(int)xh, dl = (float)(int)xl;
+                     // c_lo = c_hi 2^-16 exactly, so c_hi dh + c_lo dl =
+                     // c_hi (dh + dl 2^-16): one FFMA per state, one FMUL per beta
+                     const float d = fmaf((float)(int)xl, 0x1p-16f, (float)(int)xh);
 #pragma unroll
                      for (int j = 0; j < NB; ++j)
                          if (exact_nb || j < a.nbeta)
-                             acc[j] += ex2_approx(fmaf(dh, ch[j], dl * cl[j]));
+                             acc[j] += ex2_approx(d * ch[j]);
                  },
                  [&](unsigned) {
 #pragma unroll
@@ -220,14 +222,13 @@ __global__ void __launch_bounds__(kLzThreads) logz_walk_kernel(LzArgs a)
         // flush.  Z and the low R bits keep Kahan sums in registers, the mid
         // bits in this thread's column of shared memory (sMid).
         float acc0[NB], accTop[NB], accLo[NB][R > 1 ? R - 1 : 1], wq[NB][4];
-        float sum0[NB], comp0[NB], sumLo[NB][R], compLo[NB][R], ch[NB], cl[NB];
+        float sum0[NB], comp0[NB], sumLo[NB][R], compLo[NB][R], ch[NB];
         float *sMid = reinterpret_cast<float *>(sCl + 2 * (ns - R) * kLzThreads);
         const int nmid = ns - R;
 #pragma unroll
         for (int bb = 0; bb < NB; ++bb) {
             const float2 c2 = a.cc[(size_t)b * kLzMaxBeta + a.beta0 + bb];
             ch[bb] = c2.x;
-            cl[bb] = c2.y;
             acc0[bb] = accTop[bb] = sum0[bb] = comp0[bb] = 0.f;
 #pragma unroll
             for (int q = 0; q < 4; ++q)
@@ -245,10 +246,10 @@ __global__ void __launch_bounds__(kLzThreads) logz_walk_kernel(LzArgs a)
                  [&](unsigned xh, unsigned xl, auto U, int pi) {
                      constexpr int u = decltype(U)::value;
                      constexpr int g = u ^ (u >> 1);
-                     const float dh = (float)(int)xh, dl = (float)(int)xl;
+                     const float d = fmaf((float)(int)xl, 0x1p-16f, (float)(int)xh);
 #pragma unroll
                      for (int bb = 0; bb < NB; ++bb) {
-                         const float w = ex2_approx(fmaf(dh, ch[bb], dl * cl[bb]));
+                         const float w = ex2_approx(d * ch[bb]);
                          if constexpr (R >= 3) {
                              // aligned quads of steps: bits 2.. of the Gray code
                              // are constant over a quad, bit 0 is set at its
