@@ -31,36 +31,38 @@ __device__ double load_q(const void *Q, int dtype, int e)
     }
 }
 
-// Deterministic block sum (fixed tree) for doubles; blockDim.x must be 256.
-__device__ double block_sum_d(double x, double *red)
+// Deterministic block sum over a fixed tree, red[t] += red[t + s] for
+// s = 128, 64, ..., 1; blockDim.x must be 256.  The levels s >= 32 go through
+// shared memory, the last five through shuffles in warp 0 (the same pairs in
+// the same order, so the same result).
+template <class T>
+__device__ T block_sum_tree(T x, T *red)
 {
-    int t = threadIdx.x;
+    const int t = threadIdx.x;
     red[t] = x;
     __syncthreads();
-    for (int s = 128; s > 0; s >>= 1) {
+    for (int s = 128; s >= 32; s >>= 1) {
         if (t < s)
             red[t] = red[t] + red[t + s];
         __syncthreads();
     }
-    double r = red[0];
+    if (t < 32) {
+        T v = red[t];
+#pragma unroll
+        for (int s = 16; s > 0; s >>= 1)
+            v = v + __shfl_down_sync(0xffffffffu, v, s);
+        if (t == 0)
+            red[0] = v;
+    }
+    __syncthreads();
+    const T r = red[0];
     __syncthreads();
     return r;
 }
 
-__device__ long long block_sum_ll(long long x, long long *red)
-{
-    int t = threadIdx.x;
-    red[t] = x;
-    __syncthreads();
-    for (int s = 128; s > 0; s >>= 1) {
-        if (t < s)
-            red[t] += red[t + s];
-        __syncthreads();
-    }
-    long long r = red[0];
-    __syncthreads();
-    return r;
-}
+__device__ double block_sum_d(double x, double *red) { return block_sum_tree(x, red); }
+
+__device__ long long block_sum_ll(long long x, long long *red) { return block_sum_tree(x, red); }
 
 }  // namespace
 
@@ -197,7 +199,8 @@ __global__ void __launch_bounds__(256) prepare_kernel(const void *Q, int n, int 
 // Records and in-block corrections for a walk over suffix bits 0..ns-1 with
 // R low bits unrolled (M = ns - R mid bits, 2^M blocks).  Record B (1 <= B < 2^M)
 // describes the flip at the start of block B; entry 0 is unused.  The thread
-// with B == 0 writes the corrections K.
+// with B < 128 also writes correction K[B / 64][B % 64], so callers visit
+// every B below max(2^M, 128).
 __device__ void tables_body(const Plan *__restrict__ plan, int ns, int R, Rec *recs,
                             unsigned nrec, int *Kbuf, unsigned B)
 {
@@ -205,30 +208,26 @@ __device__ void tables_body(const Plan *__restrict__ plan, int ns, int R, Rec *r
     const int *S = plan->S;
     const int *lin = plan->lin;
 
-    if (B == 0) {
+    if (B < 128) {
         // K[pi][u]: static part of the delta at in-block step u of a block of parity pi.
-        for (int pi = 0; pi < 2; ++pi) {
-            Kbuf[pi * 64] = 0;
-            for (int u = 1; u < 64; ++u) {
-                int val = 0;
-                if (u < (1 << R)) {
-                    int l = __ffs(u) - 1;
-                    int gprev = (u - 1) ^ ((u - 1) >> 1);
-                    int gnow = u ^ (u >> 1);
-                    int nb = ((gnow >> l) & 1) ^ ((l == R - 1) ? pi : 0);
-                    unsigned corr = 0;
-                    for (int j = 0; j < R; ++j) {
-                        if (j == l)
-                            continue;
-                        int bit = (gprev >> j) & 1;
-                        int d = (j == R - 1 && pi) ? -bit : bit;
-                        corr += (unsigned)(d * S[l * n + j]);
-                    }
-                    val = (int)(nb ? corr : 0u - corr);
-                }
-                Kbuf[pi * 64 + u] = val;
+        const int pi = (int)(B >> 6), u = (int)(B & 63);
+        int val = 0;
+        if (u >= 1 && u < (1 << R)) {
+            int l = __ffs(u) - 1;
+            int gprev = (u - 1) ^ ((u - 1) >> 1);
+            int gnow = u ^ (u >> 1);
+            int nb = ((gnow >> l) & 1) ^ ((l == R - 1) ? pi : 0);
+            unsigned corr = 0;
+            for (int j = 0; j < R; ++j) {
+                if (j == l)
+                    continue;
+                int bit = (gprev >> j) & 1;
+                int d = (j == R - 1 && pi) ? -bit : bit;
+                corr += (unsigned)(d * S[l * n + j]);
             }
+            val = (int)(nb ? corr : 0u - corr);
         }
+        Kbuf[pi * 64 + u] = val;
     }
     if (B == 0 || B >= nrec)
         return;
@@ -293,7 +292,7 @@ __global__ void __launch_bounds__(256) batched_tables_kernel(const BatchDesc *de
         return;
     const BatchDesc d = desc[i];
     const unsigned nrec = 1u << (d.ns - kRMax);
-    for (unsigned B = threadIdx.x; B < nrec; B += blockDim.x)
+    for (unsigned B = threadIdx.x; B < max(nrec, 128u); B += blockDim.x)
         tables_body(plan, d.ns, kRMax, recs + d.rec_off, nrec, K + i * 128, B);
 }
 
@@ -397,7 +396,7 @@ __global__ void __launch_bounds__(256) logz_tables_kernel(const Plan *plans, int
     const int ns = w ? nsB : nsA;
     const int R = min(kRMax, ns);
     const unsigned nrec = 1u << (ns - R);
-    for (unsigned B = threadIdx.x; B < nrec; B += blockDim.x)
+    for (unsigned B = threadIdx.x; B < max(nrec, 128u); B += blockDim.x)
         tables_body(plan, ns, R, recs + (size_t)pi * rec_stride, nrec, K + pi * 128, B);
 }
 

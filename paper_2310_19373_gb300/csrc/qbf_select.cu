@@ -77,18 +77,57 @@ __global__ void __launch_bounds__(1024) threshold_kernel(const Plan *plan, const
             c->tau = INT_MAX;
         return;
     } else {
-        // smallest b with #{p : pmin[p] <= b} >= top_k
-        long long lo = c->gmin, hi = INT_MAX;
+        // smallest b with #{p : pmin[p] <= b} >= top_k, by a 16-way search:
+        // each pass counts against 15 pivots that split [lo, hi] evenly
+        // (the answer stays in [lo, hi]; hi always has count >= top_k)
+        __shared__ unsigned cnt_w[32][15];
+        __shared__ int range[2];
+        int lo = c->gmin, hi = INT_MAX;  // counts fit 32 bits: npref <= 2^28
+        const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
         while (lo < hi) {
-            const long long mid = lo + ((hi - lo) >> 1);
-            unsigned long long cnt = 0;
-            for (unsigned long long e = threadIdx.x; e < npref; e += blockDim.x)
-                cnt += ((long long)pmin[e] <= mid) ? 1ull : 0ull;
-            cnt = block_sum_u64(cnt, sh);
-            if (cnt >= (unsigned long long)top_k)
-                hi = mid;
-            else
-                lo = mid + 1;
+            const long long span = (long long)hi - lo;
+            int piv[15];
+            unsigned cnt[15];
+#pragma unroll
+            for (int j = 0; j < 15; ++j) {
+                piv[j] = (int)(lo + (span * (j + 1)) / 16);
+                cnt[j] = 0;
+            }
+            for (unsigned long long e = threadIdx.x; e < npref; e += blockDim.x) {
+                const int v = pmin[e];
+#pragma unroll
+                for (int j = 0; j < 15; ++j)
+                    cnt[j] += (v <= piv[j]) ? 1u : 0u;
+            }
+#pragma unroll
+            for (int j = 0; j < 15; ++j) {
+                unsigned x = cnt[j];
+                for (int o = 16; o > 0; o >>= 1)
+                    x += __shfl_xor_sync(0xffffffffu, x, o);
+                if (lane == 0)
+                    cnt_w[wid][j] = x;
+            }
+            __syncthreads();
+            if (threadIdx.x == 0) {
+                // (pivots recomputed, not indexed, so piv[] stays in registers)
+                int nlo = (int)(lo + (span * 15) / 16) + 1, nhi = hi;
+                for (int j = 0; j < 15; ++j) {
+                    unsigned long long tot = 0;
+                    for (int w = 0; w < nw; ++w)
+                        tot += cnt_w[w][j];
+                    if (tot >= (unsigned long long)top_k) {
+                        nhi = (int)(lo + (span * (j + 1)) / 16);
+                        nlo = j ? (int)(lo + (span * j) / 16) + 1 : lo;
+                        break;
+                    }
+                }
+                range[0] = nlo;
+                range[1] = nhi;
+            }
+            __syncthreads();
+            lo = range[0];
+            hi = range[1];
+            __syncthreads();
         }
         base = lo;
     }
@@ -139,15 +178,32 @@ __device__ __forceinline__ long long qi_at(const void *Q, int dtype, int e)
 
 // FP64 canonical order: acc = 0; for each set i ascending: row = Q_ii, then
 // row = row + (Q_ij + Q_ji) for each set j > i ascending; acc = acc + row.
-// Every add is an explicit round-to-nearest FP64 add.
-__global__ void rescore_kernel(const Plan *plan, const void *Q, int n, int dtype,
-                               const unsigned long long *cand, const Counters *c,
-                               unsigned long long cap, long long *vals)
+// Every add is an explicit round-to-nearest FP64 add.  The pair sums
+// Q_ij + Q_ji (rounded once, as in that order) and the diagonal are staged in
+// shared memory per block, so a candidate costs one add per set pair.
+__global__ void __launch_bounds__(256) rescore_kernel(const Plan *plan, const void *Q, int n,
+                                                      int dtype, const unsigned long long *cand,
+                                                      const Counters *c, unsigned long long cap,
+                                                      long long *vals)
 {
+    __shared__ long long sP[kMaxN * kMaxN];  // doubles' bits (float Q) or int64 (integer Q)
     if (plan->status != QBF_OK)
         return;
     const unsigned long long count = c->cand < cap ? c->cand : cap;
+    if ((unsigned long long)blockIdx.x * blockDim.x >= count)
+        return;  // no candidate for this block (uniform over the block)
     const bool is_int = (dtype == QBF_I32 || dtype == QBF_I16);
+    for (int e = threadIdx.x; e < n * n; e += blockDim.x) {
+        const int i = e / n, j = e % n;
+        if (j < i)
+            continue;
+        if (is_int)
+            sP[e] = (i == j) ? qi_at(Q, dtype, e) : qi_at(Q, dtype, e) + qi_at(Q, dtype, j * n + i);
+        else
+            sP[e] = __double_as_longlong(
+                (i == j) ? q_at(Q, dtype, e) : __dadd_rn(q_at(Q, dtype, e), q_at(Q, dtype, j * n + i)));
+    }
+    __syncthreads();
     for (unsigned long long e = blockIdx.x * (unsigned long long)blockDim.x + threadIdx.x;
          e < count; e += (unsigned long long)gridDim.x * blockDim.x) {
         const unsigned long long x = cand[e];
@@ -156,10 +212,10 @@ __global__ void rescore_kernel(const Plan *plan, const void *Q, int n, int dtype
             for (int i = 0; i < n; ++i) {
                 if (!((x >> i) & 1ull))
                     continue;
-                long long row = qi_at(Q, dtype, i * n + i);
+                long long row = sP[i * n + i];
                 for (int j = i + 1; j < n; ++j)
                     if ((x >> j) & 1ull)
-                        row += qi_at(Q, dtype, i * n + j) + qi_at(Q, dtype, j * n + i);
+                        row += sP[i * n + j];
                 acc += row;
             }
             vals[e] = acc;
@@ -168,11 +224,10 @@ __global__ void rescore_kernel(const Plan *plan, const void *Q, int n, int dtype
             for (int i = 0; i < n; ++i) {
                 if (!((x >> i) & 1ull))
                     continue;
-                double row = q_at(Q, dtype, i * n + i);
+                double row = __longlong_as_double(sP[i * n + i]);
                 for (int j = i + 1; j < n; ++j)
                     if ((x >> j) & 1ull)
-                        row = __dadd_rn(row, __dadd_rn(q_at(Q, dtype, i * n + j),
-                                                       q_at(Q, dtype, j * n + i)));
+                        row = __dadd_rn(row, __longlong_as_double(sP[i * n + j]));
                 acc = __dadd_rn(acc, row);
             }
             vals[e] = __double_as_longlong(acc);
@@ -205,6 +260,21 @@ __device__ __forceinline__ bool key_less(const Key &a, const Key &b, bool is_int
     return a.i < b.i;
 }
 
+// warp-wide minimum of keys (a total order: value, then index)
+__device__ __forceinline__ Key warp_min_key(Key k, bool is_int)
+{
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        Key other;
+        other.v = __shfl_xor_sync(0xffffffffu, k.v, o);
+        other.i = __shfl_xor_sync(0xffffffffu, k.i, o);
+        other.ok = __shfl_xor_sync(0xffffffffu, k.ok, o);
+        if (key_less(other, k, is_int))
+            k = other;
+    }
+    return k;
+}
+
 }  // namespace
 
 __global__ void __launch_bounds__(1024) select_kernel(const Plan *plan,
@@ -213,8 +283,8 @@ __global__ void __launch_bounds__(1024) select_kernel(const Plan *plan,
                                                       unsigned long long cap, int top_k,
                                                       DevResult *res)
 {
-    __shared__ Key sk[1024];
-    const int t = threadIdx.x;
+    __shared__ Key sk[32];
+    const int t = threadIdx.x, lane = t & 31, wid = t >> 5, nw = blockDim.x >> 5;
     if (plan->status != QBF_OK) {
         if (t == 0) {
             res->status = plan->status;
@@ -229,7 +299,11 @@ __global__ void __launch_bounds__(1024) select_kernel(const Plan *plan,
     prev.ok = 0;
     int r = 0;
     for (; r < top_k; ++r) {
+        // the smallest key above the previous winner: per thread, per warp
+        // (shuffles), then over the warps (warp 0)
         Key best;
+        best.v = 0;
+        best.i = 0;
         best.ok = 0;
         for (unsigned long long e = t; e < count; e += blockDim.x) {
             Key k;
@@ -241,13 +315,22 @@ __global__ void __launch_bounds__(1024) select_kernel(const Plan *plan,
             if (key_less(k, best, is_int))
                 best = k;
         }
-        sk[t] = best;
+        best = warp_min_key(best, is_int);
+        if (lane == 0)
+            sk[wid] = best;
         __syncthreads();
-        for (int s = blockDim.x >> 1; s > 0; s >>= 1) {
-            if (t < s && key_less(sk[t + s], sk[t], is_int))
-                sk[t] = sk[t + s];
-            __syncthreads();
+        if (wid == 0) {
+            Key k;
+            k.v = 0;
+            k.i = 0;
+            k.ok = 0;
+            if (lane < nw)
+                k = sk[lane];
+            k = warp_min_key(k, is_int);
+            if (lane == 0)
+                sk[0] = k;
         }
+        __syncthreads();
         const Key w = sk[0];
         __syncthreads();
         if (!w.ok)
