@@ -149,6 +149,8 @@ int num_sms()
 // Suffix width walked per thread when the caller leaves it to the planner:
 // small n -> few long walks are not worth it, large n -> 2^24 prefixes keep the
 // per-prefix set-up below 1% of the walk and give a fine-grained work queue.
+// (2^14 short walks at 10 < n < 24 made an n = 20 top-8 solve slower, 144 ->
+// 167 us: the top-k threshold and the flags then scan 16 times the prefixes.)
 int auto_suffix_bits(int n)
 {
     if (n <= 10)
@@ -222,6 +224,10 @@ int plan_geometry(int n, const qbf_options &o, Geo *g)
     } else {
         k = n - auto_suffix_bits(nf);
     }
+    // prefixes are numbered in 32 bits downstream (flag lists): an automatic
+    // geometry keeps at most 2^28 of them, like an explicit prefix_bits
+    if (o.prefix_bits < 0 && k > 28)
+        k = 28;
     if (o.fix_bits < 0 || o.fix_bits > n - 1)
         return set_err(QBF_EINVAL, "fix_bits must be in [0, n-1]");
     if (o.fix_bits > 0 && (o.fix_value >> o.fix_bits) != 0)
@@ -414,7 +420,7 @@ int solve_one(const void *Q, bool host_q, int n, int dtype, const qbf_options *o
     // W from the plan, so the host sizes the grid for the general case.
     {
         const int fb = (int)std::min<unsigned long long>((npref + 255) / 256, 4096);
-        flag_kernel<<<fb, 256, 0, s>>>(plan, pmin, npref, g.p_lo, o.top_k, flagged, ctr);
+        flag_kernel<<<fb, 256, 0, s>>>(plan, pmin, npref, o.top_k, flagged, ctr);
         QBF_CUDA(cudaGetLastError(), "flag_kernel");
     }
     WalkArgs e = a;

@@ -54,7 +54,7 @@ __global__ void reset_counters_kernel(Counters *c);
 __global__ void threshold_kernel(const Plan *plan, const int *pmin, unsigned long long npref,
                                  int top_k, Counters *c);
 __global__ void flag_kernel(const Plan *plan, const int *pmin, unsigned long long npref,
-                            unsigned long long p_lo, int top_k, unsigned int *flagged, Counters *c);
+                            int top_k, unsigned int *flagged, Counters *c);
 __global__ void rescore_kernel(const Plan *plan, const void *Q, int n, int dtype,
                                const unsigned long long *cand, const Counters *c,
                                unsigned long long cap, long long *vals);

@@ -208,7 +208,7 @@ int solve_noalloc_locked(const void *Q, int n, int dtype, const qbf_options *opt
     NA_CUDA(cudaGetLastError(), "threshold_kernel launch failed");
     const bool is_int = (dtype == QBF_I32 || dtype == QBF_I16);
     const int fb = (int)std::min<unsigned long long>((npref + 255) / 256, 4096);
-    flag_kernel<<<fb, 256, 0, s>>>(plan, pmin, npref, p_lo, o.top_k, flagged, ctr);
+    flag_kernel<<<fb, 256, 0, s>>>(plan, pmin, npref, o.top_k, flagged, ctr);
     NA_CUDA(cudaGetLastError(), "flag_kernel launch failed");
     WalkArgs e = a;
     e.ns = ns - q;

@@ -11,7 +11,8 @@
 //                     fixed-point values are <= tau - W.
 //   flag_kernel       lists the prefixes with pmin <= tau (or, for a top-1
 //                     solve with exact values, W = 0, only the lowest such
-//                     prefix: its lowest tied state has the lowest index).
+//                     prefix: its lowest tied state has the lowest index),
+//                     numbered from p_lo.
 //   rescore_kernel    evaluates every emitted candidate state from the
 //                     caller's Q: the FP64 canonical sum for float Q (the
 //                     order every FP64 value in this project uses), the exact
@@ -81,6 +82,7 @@ __global__ void __launch_bounds__(1024) threshold_kernel(const Plan *plan, const
         // each pass counts against 15 pivots that split [lo, hi] evenly
         // (the answer stays in [lo, hi]; hi always has count >= top_k)
         __shared__ unsigned cnt_w[32][15];
+        __shared__ unsigned long long tot_s[15];
         __shared__ int range[2];
         int lo = c->gmin, hi = INT_MAX;  // counts fit 32 bits: npref <= 2^28
         const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
@@ -108,14 +110,18 @@ __global__ void __launch_bounds__(1024) threshold_kernel(const Plan *plan, const
                     cnt_w[wid][j] = x;
             }
             __syncthreads();
+            if (threadIdx.x < 15) {  // one thread per pivot sums the warps' counts
+                unsigned long long tot = 0;
+                for (int w = 0; w < nw; ++w)
+                    tot += cnt_w[w][threadIdx.x];
+                tot_s[threadIdx.x] = tot;
+            }
+            __syncthreads();
             if (threadIdx.x == 0) {
                 // (pivots recomputed, not indexed, so piv[] stays in registers)
                 int nlo = (int)(lo + (span * 15) / 16) + 1, nhi = hi;
                 for (int j = 0; j < 15; ++j) {
-                    unsigned long long tot = 0;
-                    for (int w = 0; w < nw; ++w)
-                        tot += cnt_w[w][j];
-                    if (tot >= (unsigned long long)top_k) {
+                    if (tot_s[j] >= (unsigned long long)top_k) {
                         nhi = (int)(lo + (span * (j + 1)) / 16);
                         nlo = j ? (int)(lo + (span * j) / 16) + 1 : lo;
                         break;
@@ -138,7 +144,7 @@ __global__ void __launch_bounds__(1024) threshold_kernel(const Plan *plan, const
 }
 
 __global__ void flag_kernel(const Plan *plan, const int *pmin, unsigned long long npref,
-                            unsigned long long p_lo, int top_k, unsigned int *flagged, Counters *c)
+                            int top_k, unsigned int *flagged, Counters *c)
 {
     if (plan->status != QBF_OK)
         return;
@@ -147,7 +153,9 @@ __global__ void flag_kernel(const Plan *plan, const int *pmin, unsigned long lon
     for (unsigned long long e = blockIdx.x * (unsigned long long)blockDim.x + threadIdx.x;
          e < npref; e += (unsigned long long)gridDim.x * blockDim.x) {
         if (pmin[e] <= tau) {
-            const unsigned p = (unsigned)(p_lo + e);
+            // relative to p_lo (e < npref <= 2^28): fixed sub-spaces may sit
+            // above 2^32 in absolute prefix numbers
+            const unsigned p = (unsigned)e;
             if (lowest_mode)
                 atomicMin(&c->lowest, p);
             else

@@ -106,8 +106,9 @@ __global__ void __launch_bounds__(kWalkThreads) walk_split_kernel(const Plan *__
             unsigned long long i = item * 32 + lane;
             active = i < total;
             unsigned long long ic = active ? i : total - 1;
-            unsigned long long fp = lowest_mode ? (unsigned long long)a.ctr->lowest
-                                                : (unsigned long long)a.flagged[ic >> a.q];
+            // flagged prefixes are numbered from p_lo (the MIN walk's range)
+            unsigned long long fp = a.p_lo + (lowest_mode ? (unsigned long long)a.ctr->lowest
+                                                          : (unsigned long long)a.flagged[ic >> a.q]);
             p = (fp << a.q) | (ic & ((1ull << a.q) - 1));
         } else {
             unsigned long long i = a.p_lo + item * 32 + lane;

@@ -268,6 +268,22 @@ def test_block_count_limit(variant, n_ok):
     assert e.value.status == qb.QBF_EINVAL
 
 
+@pytest.mark.parametrize("n,fix", [(46, 28), (48, 34), (44, 24)])
+def test_large_fix_keeps_prefix_numbers_in_range(n, fix):
+    """With most variables fixed, prefix numbers pass 2^32: the automatic
+    geometry would give k = 37 at n = 46, fix 28 (the planner caps it at 28),
+    and fix_bits = 34 makes the prefix the fixed part itself (k = 34).  The
+    flag list numbers prefixes from the sub-space's first one, so the fixed
+    sub-space still matches the oracle."""
+    Q = inputs.gaussian_f32(n, seed=n + fix)
+    rng = np.random.default_rng(fix)
+    for fv in [int(v) for v in rng.integers(0, 1 << fix, size=2)]:
+        sol = qb.solve(dev(Q), fix_bits=fix, fix_value=fv)
+        lo = fv << (n - fix)
+        assert (sol.min_value, sol.argmin) == oracle.brute_min(Q, lo, lo + (1 << (n - fix)))
+        assert sol.prefix_bits == max(28, fix)
+
+
 def test_host_pointer_path_matches_device_path():
     Q = inputs.config_n20_f64(0)
     a = qb.solve(dev(Q), top_k=8)
