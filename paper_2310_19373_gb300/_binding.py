@@ -21,8 +21,8 @@ QBF_EOVERFLOW, QBF_ECANCELED, QBF_ENOTIMPL, QBF_ERANGE = 5, 6, 7, 8
 QBF_VARIANT_AUTO, QBF_VARIANT_FIELD, QBF_VARIANT_SPLIT, QBF_VARIANT_TC = 0, 1, 2, 3
 QBF_VARIANT_SPLIT_F32 = 4
 QBF_VARIANT_SPLIT_MIX = 5
-QBF_VARIANT_SPLIT_DEFER = 7
 QBF_VARIANT_NAIVE = 6
+QBF_VARIANT_SPLIT_DEFER = 7
 QBF_MAX_N = 48
 QBF_MAX_TOPK = 64
 

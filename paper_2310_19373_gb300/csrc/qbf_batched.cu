@@ -7,7 +7,10 @@
 // atomic counter; each warp keeps the current instance's int32 image (S, lin)
 // and its in-block corrections in its own slice of shared memory and reloads
 // them only when it moves to another instance.  ns_i is the same for all large
-// instances, so items cost about the same and the tail is one item.
+// instances, so items cost about the same and the tail is one item.  An item
+// of an instance whose fixed-point image fits 2^23 runs the deferred-correction
+// walk (qbf_walk_defer_core.cuh; AUTO) or the two-pipe walk, the others the
+// int32 walk.
 //
 // Certification per instance is the single-instance rule (qbf_select.cu):
 // every item whose minimum is within W_i of instance i's minimum is re-walked,
