@@ -381,14 +381,17 @@ int qbf_walk_trace(const void *Q_dev, int n, int dtype, int prefix_bits, uint64_
 /*
  * qbf_prefix_minima -- the MIN kernel alone, exposing its per-prefix minima.
  *
- * Runs the production MIN kernel of `variant` (QBF_VARIANT_SPLIT / AUTO: the
- * Gray walk with 2^prefix_bits threads; QBF_VARIANT_TC: the tensor-core blocked
- * form, which requires prefix_bits = n - 14) over the whole space and writes,
- * for every prefix p (the top prefix_bits variables), the minimum over its
- * 2^(n - prefix_bits) suffix states of the fixed-point objective
- * round(Q * 2^sigma) to pmin_dev[p] (int32, 2^prefix_bits entries,
- * caller-owned device memory).  *sigma_out receives sigma.  1 <= n <= 48,
- * 0 <= prefix_bits <= min(n-1, 28).  Used to test the kernels prefix by prefix
+ * Runs the production MIN kernel of `variant` over the whole space:
+ * QBF_VARIANT_SPLIT / AUTO the int32 Gray walk with 2^prefix_bits threads;
+ * SPLIT_F32, SPLIT_MIX, SPLIT_DEFER the FP32-image walks (a thread takes 2 or
+ * 8 prefixes that differ in their lowest prefix variables); FIELD and NAIVE
+ * the reference forms; TC the tensor-core blocked form, which requires
+ * prefix_bits = n - 14.  For every prefix p (the top prefix_bits variables) it
+ * writes the minimum over its 2^(n - prefix_bits) suffix states of the
+ * fixed-point objective round(Q * 2^sigma) to pmin_dev[p] (int32,
+ * 2^prefix_bits entries, caller-owned device memory).  *sigma_out receives
+ * sigma.  1 <= n <= 48, 0 <= prefix_bits <= min(n-1, 28), plus each variant's
+ * limits (QBF_EINVAL otherwise).  Used to test the kernels prefix by prefix
  * against the oracle.
  */
 int qbf_prefix_minima(const void *Q_dev, int n, int dtype, int prefix_bits, int variant,
