@@ -383,8 +383,8 @@ int qbf_walk_trace(const void *Q_dev, int n, int dtype, int prefix_bits, uint64_
  *
  * Runs the production MIN kernel of `variant` over the whole space:
  * QBF_VARIANT_SPLIT / AUTO the int32 Gray walk with 2^prefix_bits threads;
- * SPLIT_F32, SPLIT_MIX, SPLIT_DEFER the FP32-image walks (a thread takes 2 or
- * 8 prefixes that differ in their lowest prefix variables); FIELD and NAIVE
+ * SPLIT_F32, SPLIT_MIX, SPLIT_DEFER the FP32-image walks (a thread walks 2 or
+ * 8 values at once: its pair or group bits are the top suffix bits); FIELD and NAIVE
  * the reference forms; TC the tensor-core blocked form, which requires
  * prefix_bits = n - 14.  For every prefix p (the top prefix_bits variables) it
  * writes the minimum over its 2^(n - prefix_bits) suffix states of the
