@@ -16,6 +16,9 @@ Functions
 evaluate(Q, idx)          f at one state (or an array of states)
 brute_min(Q, lo, hi)      (min f, lowest argmin idx) over idx in [lo, hi)
 brute_topk(Q, k, lo, hi)  k smallest (value, idx) pairs, lexicographic
+blocked_topk(Q, k, lo, hi) brute_topk's answer by the blocked walk (n up to 62)
+blocked_min(Q, lo, hi)    brute_min's answer by the blocked walk
+segment_minima(Q, seg, nseg, lo)  per-segment minima by the blocked walk
 logz(Q, betas)            log sum_x exp(-beta f(x)) and E_beta[x x^T] (FP64)
 ising_from_qubo(Q)        the textbook QUBO -> Ising change of variables
 ising_energy(J, h, c, s)  energy of spins s in {-1,+1}^n
@@ -63,6 +66,19 @@ def _load():
         lib.orc_logz_f64.restype = ctypes.c_int
         lib.orc_logz_f64.argtypes = [c_dp, ctypes.c_int, c_dp, ctypes.c_int, ctypes.c_int,
                                      c_dp, c_dp, c_dp, c_up]
+        c_u64 = ctypes.c_uint64
+        lib.orc_topk_blocked_f64.restype = ctypes.c_int
+        lib.orc_topk_blocked_f64.argtypes = [c_dp, ctypes.c_int, c_u64, c_u64, ctypes.c_int,
+                                             ctypes.c_int, c_dp, c_up, c_up]
+        lib.orc_topk_blocked_i64.restype = ctypes.c_int
+        lib.orc_topk_blocked_i64.argtypes = [c_ip, ctypes.c_int, c_u64, c_u64, ctypes.c_int,
+                                             ctypes.c_int, c_ip, c_up]
+        lib.orc_segmin_blocked_f64.restype = ctypes.c_int
+        lib.orc_segmin_blocked_f64.argtypes = [c_dp, ctypes.c_int, c_u64, c_u64, c_u64,
+                                               ctypes.c_int, c_dp, c_up]
+        lib.orc_segmin_blocked_i64.restype = ctypes.c_int
+        lib.orc_segmin_blocked_i64.argtypes = [c_ip, ctypes.c_int, c_u64, c_u64, c_u64,
+                                               ctypes.c_int, c_ip, c_up]
         lib.orc_default_threads.restype = ctypes.c_int
         lib.orc_default_threads.argtypes = []
         _lib = lib
@@ -148,6 +164,76 @@ def brute_topk(Q, k: int, lo: int = 0, hi: int | None = None, threads: int = 0):
     if cnt < 0:
         raise ValueError("oracle brute_topk: bad arguments")
     return vals[:cnt], ix[:cnt]
+
+
+_BLOCKED_ERR = {-1: "bad arguments (range, k, n > 62, non-finite or oversized Q)",
+                -2: "out of memory",
+                -3: "more than 2^24 near-tied candidate states in one thread"}
+
+
+def blocked_topk(Q, k: int, lo: int = 0, hi: int | None = None, threads: int = 0,
+                 return_candidates: bool = False):
+    """The k smallest states by (value, idx) -- brute_topk's answer -- computed by
+    the blocked natural-order walk (qubo_oracle_blocked.c), for n up to 62.
+
+    Float Q: the blocked FP64 values only select candidates (every state within
+    the rigorous rounding bound of the running k-th best); the returned values
+    are the canonical FP64 values of those candidates.  Integer Q: exact int64.
+    With ``return_candidates`` also returns the number of states re-evaluated.
+    """
+    lib = _load()
+    Qm, is_int = _as_matrix(Q)
+    n = Qm.shape[0]
+    if hi is None:
+        hi = 1 << n
+    ix = np.zeros(k, dtype=np.uint64)
+    ncand = ctypes.c_uint64(0)
+    if is_int:
+        vals = np.zeros(k, dtype=np.int64)
+        cnt = lib.orc_topk_blocked_i64(_ptr(Qm, ctypes.c_int64), n, lo, hi, k, threads,
+                                       _ptr(vals, ctypes.c_int64), _ptr(ix, ctypes.c_uint64))
+    else:
+        vals = np.zeros(k, dtype=np.float64)
+        cnt = lib.orc_topk_blocked_f64(_ptr(Qm, ctypes.c_double), n, lo, hi, k, threads,
+                                       _ptr(vals, ctypes.c_double), _ptr(ix, ctypes.c_uint64),
+                                       ctypes.byref(ncand))
+    if cnt < 0:
+        raise ValueError("oracle blocked_topk: " + _BLOCKED_ERR.get(cnt, str(cnt)))
+    if return_candidates:
+        return vals[:cnt], ix[:cnt], int(ncand.value)
+    return vals[:cnt], ix[:cnt]
+
+
+def blocked_min(Q, lo: int = 0, hi: int | None = None, threads: int = 0):
+    """(min value, lowest argmin idx) over [lo, hi) -- brute_min's answer -- by the
+    blocked natural-order walk."""
+    vals, ix = blocked_topk(Q, 1, lo, hi, threads)
+    v = vals[0].item()
+    return v, int(ix[0])
+
+
+def segment_minima(Q, seg: int, nseg: int, lo: int = 0, threads: int = 0):
+    """Minimum and lowest argmin of each segment [lo + s*seg, lo + (s+1)*seg),
+    s < nseg, by the blocked walk (one segment per thread at a time).
+
+    Returns (values[nseg], indices[nseg]); values are int64 for integer Q and
+    canonical FP64 for float Q.
+    """
+    lib = _load()
+    Qm, is_int = _as_matrix(Q)
+    n = Qm.shape[0]
+    ix = np.zeros(nseg, dtype=np.uint64)
+    if is_int:
+        vals = np.zeros(nseg, dtype=np.int64)
+        rc = lib.orc_segmin_blocked_i64(_ptr(Qm, ctypes.c_int64), n, lo, seg, nseg, threads,
+                                        _ptr(vals, ctypes.c_int64), _ptr(ix, ctypes.c_uint64))
+    else:
+        vals = np.zeros(nseg, dtype=np.float64)
+        rc = lib.orc_segmin_blocked_f64(_ptr(Qm, ctypes.c_double), n, lo, seg, nseg, threads,
+                                        _ptr(vals, ctypes.c_double), _ptr(ix, ctypes.c_uint64))
+    if rc != 0:
+        raise ValueError("oracle segment_minima: " + _BLOCKED_ERR.get(rc, str(rc)))
+    return vals, ix
 
 
 def logz(Q, betas, moment: bool = True, threads: int = 0):

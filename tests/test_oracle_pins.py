@@ -299,3 +299,88 @@ def test_logz_moment_matches_central_differences():
             fd = (oracle.logz(Qp, [beta], moment=False)[0][0] -
                   oracle.logz(Qm, [beta], moment=False)[0][0]) / (2 * h)
             assert abs(fd - (-beta * E[0][i, j])) <= 1e-5 * max(1e-3, abs(beta * E[0][i, j]))
+
+
+# ---------------------------------------------------------------- blocked natural-order walk
+
+
+def _literal_vs_blocked(Q, k, lo, hi, threads):
+    a = oracle.brute_topk(Q, k, lo, hi)
+    b = oracle.blocked_topk(Q, k, lo, hi, threads=threads)
+    assert np.array_equal(a[0], b[0]) and np.array_equal(a[1], b[1]), (k, lo, hi, a, b)
+
+
+@pytest.mark.parametrize("seed", range(6))
+def test_blocked_walk_equals_literal_oracle(seed):
+    """The blocked walk (the large-n oracle) returns the literal loop's top-k bit
+    for bit: float Q in canonical FP64, integer Q exactly, with many exact ties
+    (small integer ranges, integer-valued floats), on ragged index ranges and
+    for thread counts that split blocks unevenly."""
+    rng = np.random.default_rng(5000 + seed)
+    for trial in range(12):
+        n = int(rng.integers(1, 21))
+        kind = trial % 4
+        if kind == 0:
+            Q = rng.integers(-3, 4, size=(n, n))
+        elif kind == 1:
+            Q = np.triu(rng.normal(size=(n, n)))
+        elif kind == 2:
+            Q = rng.integers(-1, 2, size=(n, n)).astype(np.float64)  # exact float ties
+        else:
+            Q = rng.uniform(-1, 1, size=(n, n)).astype(np.float32)
+        N = 1 << n
+        lo = int(rng.integers(0, N))
+        hi = int(rng.integers(lo + 1, N + 1))
+        if trial % 3 == 0:
+            lo, hi = 0, N
+        _literal_vs_blocked(Q, int(rng.integers(1, 40)), lo, hi, int(rng.integers(1, 9)))
+
+
+def test_blocked_walk_hand_tables_and_closed_forms():
+    """The hand-worked n = 2, 3 tables, the diagonal closed form and the all-zero
+    matrix (every state ties at 0, lowest indices first) through the blocked walk."""
+    for name in ("hand_n2.json", "hand_n3.json"):
+        g = _load(name)
+        for Q in (np.array(g["Q"], dtype=np.int64), np.array(g["Q"], dtype=np.float64)):
+            v, am = oracle.blocked_min(Q)
+            assert (v, am) == (g["min"], g["argmin"])
+    d = np.random.default_rng(3).uniform(-1, 1, size=22)
+    v, am = oracle.blocked_min(np.diag(d))
+    assert am == sum(1 << i for i in range(22) if d[i] < 0)
+    assert abs(v - np.minimum(d, 0).sum()) <= 1e-14 * 22
+    for Z in (np.zeros((23, 23)), np.zeros((23, 23), dtype=np.int32)):
+        vals, ix = oracle.blocked_topk(Z, 4)
+        assert list(ix) == [0, 1, 2, 3] and list(vals) == [0, 0, 0, 0]
+
+
+@pytest.mark.parametrize("n", [22, 24])
+def test_blocked_walk_at_larger_n(n):
+    """Past the 2^12-state block: several high parts per thread, top-8, against the
+    literal loop (float and integer with ties)."""
+    rng = np.random.default_rng(6000 + n)
+    for Q in (np.triu(rng.normal(size=(n, n))).astype(np.float32),
+              rng.integers(-2, 3, size=(n, n)).astype(np.int16)):
+        _literal_vs_blocked(Q, 8, 0, 1 << n, 0)
+
+
+def test_segment_minima_equal_range_minima():
+    """Per-segment minima (the per-prefix minima of a walk with the top bits as
+    the prefix) equal brute_min over each segment."""
+    rng = np.random.default_rng(61)
+    for Q in (rng.integers(-50, 51, size=(17, 17)), np.triu(rng.normal(size=(17, 17)))):
+        for seg, nseg, lo in ((1 << 13, 16, 0), (1 << 9, 40, 3 << 9), (1, 20, 777)):
+            v, ix = oracle.segment_minima(Q, seg, nseg, lo)
+            for s in range(nseg):
+                assert (v[s], ix[s]) == oracle.brute_min(Q, lo + s * seg, lo + (s + 1) * seg)
+
+
+def test_blocked_walk_catches_planted_mistakes():
+    """A dropped lower part or a wrong sign in Q changes the blocked answer on an
+    instance whose literal answer is known, so the comparison above has teeth."""
+    rng = np.random.default_rng(62)
+    n = 15
+    Q = rng.integers(-9, 10, size=(n, n))
+    ref = oracle.brute_topk(Q, 5)
+    for bad in (np.triu(Q), Q - 2 * np.diag(np.diag(Q))):
+        got = oracle.blocked_topk(bad, 5)
+        assert not (np.array_equal(ref[0], got[0]) and np.array_equal(ref[1], got[1]))
