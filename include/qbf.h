@@ -113,8 +113,10 @@ typedef struct {
 } qbf_options;
 
 typedef struct {
-    double min_value;   /* min f; FP64 canonical sum for float Q, exact for
-                           integer Q (see README of the oracle order)       */
+    double min_value;   /* min f; FP64 canonical sum for float Q (rows i
+                           ascending, row = Q_ii + sum_{j>i} (Q_ij + Q_ji)
+                           in ascending j, rows added in order), exact for
+                           integer Q                                        */
     uint64_t argmin;    /* lowest natural index attaining min_value         */
     int top_k;          /* entries filled in topk_* (<= requested)          */
     double topk_value[QBF_MAX_TOPK];   /* ascending by (value, index)       */
@@ -396,6 +398,29 @@ int qbf_walk_trace(const void *Q_dev, int n, int dtype, int prefix_bits, uint64_
  */
 int qbf_prefix_minima(const void *Q_dev, int n, int dtype, int prefix_bits, int variant,
                       int32_t *pmin_dev, int *sigma_out, void *stream);
+
+/*
+ * qbf_prefix_minima_fixed -- qbf_prefix_minima over a window of prefixes.
+ *
+ * Section 3.1's split with its top fix_bits prefix variables fixed: the MIN
+ * kernel of `variant` runs in the geometry a solve with prefix_bits prefix
+ * variables uses (same suffix width, block records and in-block unrolling),
+ * but only over the 2^(prefix_bits - fix_bits) prefixes p whose top fix_bits
+ * bits equal fix_value, i.e. the natural indices
+ *     [fix_value * 2^(n - fix_bits), (fix_value + 1) * 2^(n - fix_bits)).
+ * pmin_dev[j] (int32, 2^(prefix_bits - fix_bits) entries, caller-owned device
+ * memory) receives the minimum of round(Q * 2^sigma) over prefix
+ * p = fix_value * 2^(prefix_bits - fix_bits) + j, whose states are the natural
+ * indices [p * 2^(n - prefix_bits), (p + 1) * 2^(n - prefix_bits)).  sigma is
+ * that of the whole problem (the same image as a full solve).  Requires
+ * 0 <= fix_bits <= prefix_bits and fix_value < 2^fix_bits, plus
+ * qbf_prefix_minima's limits (QBF_EINVAL otherwise).  Lets a test check the
+ * kernels prefix by prefix at the full walk depth of a large solve without
+ * walking all of its prefixes.
+ */
+int qbf_prefix_minima_fixed(const void *Q_dev, int n, int dtype, int prefix_bits, int variant,
+                            int fix_bits, uint64_t fix_value, int32_t *pmin_dev, int *sigma_out,
+                            void *stream);
 
 /*
  * qbf_tc_selftest -- one tcgen05 MMA on given operands: D = A * B with A

@@ -143,6 +143,9 @@ _SIGS = {
                                       ctypes.POINTER(ctypes.c_int), _VP]),
     "qbf_prefix_minima": (ctypes.c_int, [_VP, ctypes.c_int, ctypes.c_int, ctypes.c_int,
                                          ctypes.c_int, _VP, ctypes.POINTER(ctypes.c_int), _VP]),
+    "qbf_prefix_minima_fixed": (ctypes.c_int, [_VP, ctypes.c_int, ctypes.c_int, ctypes.c_int,
+                                               ctypes.c_int, ctypes.c_int, ctypes.c_uint64, _VP,
+                                               ctypes.POINTER(ctypes.c_int), _VP]),
     "qbf_tc_selftest": (ctypes.c_int, [_VP, _VP, _VP]),
     "qbf_alu_microbench": (ctypes.c_int, [ctypes.c_int, ctypes.POINTER(ctypes.c_double),
                                           ctypes.POINTER(ctypes.c_double),
@@ -356,6 +359,17 @@ def qbf_prefix_minima(Q_dev: int, n: int, dtype: int, prefix_bits: int, variant:
     return sigma.value
 
 
+def qbf_prefix_minima_fixed(Q_dev: int, n: int, dtype: int, prefix_bits: int, variant: int,
+                            fix_bits: int, fix_value: int, pmin_dev: int,
+                            stream: int | None = None) -> int:
+    sigma = ctypes.c_int()
+    rc = lib().qbf_prefix_minima_fixed(_VP(Q_dev), n, dtype, prefix_bits, variant, fix_bits,
+                                       fix_value, _VP(pmin_dev), ctypes.byref(sigma),
+                                       _VP(stream or 0))
+    _check(rc)
+    return sigma.value
+
+
 def qbf_tc_selftest(A_fp16_bits, B_fp16_bits):
     """A: 128x16, B: 16x128 uint16 arrays of FP16 bit patterns (numpy); returns D 128x128."""
     import numpy as np
@@ -546,6 +560,20 @@ def prefix_minima(Q, prefix_bits: int, variant: int = QBF_VARIANT_AUTO):
     s = torch.cuda.current_stream(Q.device).cuda_stream
     sigma = qbf_prefix_minima(Q.data_ptr(), n, dtype_code(Q), prefix_bits, variant,
                               pm.data_ptr(), s)
+    return pm, sigma
+
+
+def prefix_minima_fixed(Q, prefix_bits: int, fix_bits: int, fix_value: int,
+                        variant: int = QBF_VARIANT_AUTO):
+    """Per-prefix minima over the prefixes under the top fix_bits = fix_value, and sigma."""
+    import torch
+
+    Q = Q.contiguous()
+    n = Q.shape[0]
+    pm = torch.empty(1 << (prefix_bits - fix_bits), dtype=torch.int32, device=Q.device)
+    s = torch.cuda.current_stream(Q.device).cuda_stream
+    sigma = qbf_prefix_minima_fixed(Q.data_ptr(), n, dtype_code(Q), prefix_bits, variant,
+                                    fix_bits, fix_value, pm.data_ptr(), s)
     return pm, sigma
 
 

@@ -841,8 +841,9 @@ int qbf_walk_trace(const void *Q_dev, int n, int dtype, int prefix_bits, uint64_
     return QBF_OK;
 }
 
-int qbf_prefix_minima(const void *Q_dev, int n, int dtype, int prefix_bits, int variant,
-                      int32_t *pmin_dev, int *sigma_out, void *stream)
+static int prefix_minima_impl(const void *Q_dev, int n, int dtype, int prefix_bits, int variant,
+                              int fix_bits, uint64_t fix_value, int32_t *pmin_dev, int *sigma_out,
+                              void *stream)
 {
     std::lock_guard<std::mutex> lk(g_mu);
     cudaStream_t s = (cudaStream_t)stream;
@@ -859,10 +860,16 @@ int qbf_prefix_minima(const void *Q_dev, int n, int dtype, int prefix_bits, int 
         variant != QBF_VARIANT_FIELD && variant != QBF_VARIANT_NAIVE &&
         variant != QBF_VARIANT_SPLIT_DEFER)
         return set_err(QBF_ENOTIMPL, "requested walk variant is not built");
+    if (fix_bits < 0 || fix_bits > prefix_bits)
+        return set_err(QBF_EINVAL, "fix_bits must be in [0, prefix_bits]");
+    if (fix_bits < 64 && (fix_value >> fix_bits) != 0)
+        return set_err(QBF_EINVAL, "fix_value has bits above fix_bits");
     qbf_options o;
     qbf_default_options(&o);
     o.prefix_bits = prefix_bits;
     o.variant = variant;
+    o.fix_bits = fix_bits;
+    o.fix_value = fix_value;
     const bool tc = (variant == QBF_VARIANT_TC);
     const bool mix = (variant == QBF_VARIANT_SPLIT_MIX);
     const bool defer = (variant == QBF_VARIANT_SPLIT_DEFER);
@@ -926,6 +933,21 @@ int qbf_prefix_minima(const void *Q_dev, int n, int dtype, int prefix_bits, int 
         return set_err(PH->status, "prepare failed");
     *sigma_out = PH->sigma;
     return QBF_OK;
+}
+
+int qbf_prefix_minima(const void *Q_dev, int n, int dtype, int prefix_bits, int variant,
+                      int32_t *pmin_dev, int *sigma_out, void *stream)
+{
+    return prefix_minima_impl(Q_dev, n, dtype, prefix_bits, variant, 0, 0, pmin_dev, sigma_out,
+                              stream);
+}
+
+int qbf_prefix_minima_fixed(const void *Q_dev, int n, int dtype, int prefix_bits, int variant,
+                            int fix_bits, uint64_t fix_value, int32_t *pmin_dev, int *sigma_out,
+                            void *stream)
+{
+    return prefix_minima_impl(Q_dev, n, dtype, prefix_bits, variant, fix_bits, fix_value,
+                              pmin_dev, sigma_out, stream);
 }
 
 int qbf_tc_selftest(const uint16_t *A_host, const uint16_t *B_host, float *D_host)
