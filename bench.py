@@ -115,24 +115,136 @@ class ClockSampler:
                 "samples": len(rows)}
 
 
-def cpu_baseline(Q, target_s=12.0):
-    """Time the CPU oracle (as it stands) on a bounded sample of the same instance."""
+def cpu_model():
+    """The host CPU's model name and core count (lscpu, else /proc/cpuinfo)."""
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.startswith("Model name:"):
+                return line.split(":", 1)[1].strip()
+    except (OSError, subprocess.SubprocessError):
+        pass
+    try:
+        with open("/proc/cpuinfo") as f:
+            for line in f:
+                if line.lower().startswith(("model name", "cpu part")):
+                    return line.split(":", 1)[1].strip()
+    except OSError:
+        pass
+    return "unknown"
+
+
+def random_windows(n, bits, count, seed):
+    """`count` distinct aligned windows of 2^bits natural indices at random high
+    prefixes: the sample spans the whole index range, so the set bits per
+    state (which the oracle's per-state cost follows) match the full walk."""
+    import numpy as np
+
+    rng = np.random.default_rng(seed)
+    hi = 1 << (n - bits)
+    w = rng.choice(hi, size=min(count, hi), replace=False)
+    return [(int(v) << bits, (int(v) + 1) << bits) for v in w]
+
+
+def cpu_baseline(Q, target_s=12.0, seed=0):
+    """Time the CPU oracle (as it stands) on a bounded sample of the same instance:
+    whole 2^22-state windows at random high prefixes, until about target_s."""
     import oracle
 
     cores = oracle.threads_default()
     bits = 22
+    wins = random_windows(N_VARS, bits, 4096, seed)
+    done, dt = 0, 0.0
+    for lo, hi in wins:
+        t0 = time.perf_counter()
+        oracle.brute_min(Q, lo, hi)
+        dt += time.perf_counter() - t0
+        done += 1
+        if dt >= target_s:
+            break
+    return {"value": done * (1 << bits) / dt, "unit": "states/s", "cores": cores, "kind": "oracle",
+            "cpu_model": cpu_model(),
+            "sample": f"natural-order FP64 brute force over {done} windows of 2^{bits} states at "
+                      f"random high prefixes of the n=40 instance (seed {seed}), {dt:.1f} s"}
+
+
+def cpu_gray_baseline(Q, target_s=6.0):
+    """The paper's CPU design on the same cores: Algorithm 1 (Eq. 2's O(n) delta
+    from the row of the flipped variable) with the prefix threads of Section
+    3.1, FP64, written fresh (cpu_baseline/cpu_gray.c).  Timed on random
+    prefixes of the n=40 instance; the paper's own figure is n = 30 in under
+    4 s on an Intel i7-8700 (at least 2.7e8 states/s)."""
+    import numpy as np
+
+    import cpu_baseline as cg
+
+    m = 16
+    rng = np.random.default_rng(1)
+    pre = rng.choice(1 << m, size=16, replace=False)
     t0 = time.perf_counter()
-    oracle.brute_min(Q, 0, 1 << bits)
+    _, _, T = cg.walk(Q, m, pre)
     dt = time.perf_counter() - t0
-    while dt * 2 < target_s and bits < N_VARS:
-        bits += 1
-        dt *= 2
+    per = 16 * 2.0 ** (N_VARS - m) / dt
+    count = max(16, min(1 << m, int(16 * target_s / max(dt, 1e-3))))
+    pre = rng.choice(1 << m, size=count, replace=False)
     t0 = time.perf_counter()
-    oracle.brute_min(Q, 0, 1 << bits)
+    _, _, T = cg.walk(Q, m, pre)
     dt = time.perf_counter() - t0
-    return {"value": (1 << bits) / dt, "unit": "states/s", "cores": cores, "kind": "oracle",
-            "sample": f"natural-order FP64 brute force over the first 2^{bits} states of the "
-                      f"n=40 instance (top {N_VARS - bits} bits zero), {dt:.1f} s"}
+    rate = count * 2.0 ** (N_VARS - m) / dt
+    return {"value": rate, "unit": "states/s", "cores": T, "cpu_model": cpu_model(),
+            "kind": "Algorithm 1 + Section 3.1 prefix threads, FP64 (the paper's CPU design)",
+            "sample": f"{count} prefixes of the top {m} variables (2^{N_VARS - m} states each) of "
+                      f"the n=40 instance, {dt:.1f} s",
+            "n30_seconds_at_this_rate": 2.0 ** 30 / rate,
+            "paper_context": "n=30 in < 4 s on an Intel i7-8700 (Section 4): >= 2.7e8 states/s"}
+
+
+def oracle_timings():
+    """The CPU oracle on the other configurations, on the host cores: n=20 FP64
+    top-8 in full (literal loop); n=32 int32 dense and 50% sparse in full
+    (blocked walk) and the literal loop's rate on random windows; the literal
+    loop's rate on an n=28 log Z instance, scaled to the 64-instance, 3-beta
+    forward pass; the blocked walk at n=40 on a 2^34-state sample scaled to
+    the whole space."""
+    import oracle
+    from paper_2310_19373_gb300 import inputs
+
+    out = {"cores": oracle.threads_default(), "cpu_model": cpu_model()}
+    t0 = time.perf_counter()
+    oracle.brute_topk(inputs.config_n20_f64(0), 8)
+    out["n20_f64_top8_literal_s"] = time.perf_counter() - t0
+    for sparse in (False, True):
+        Q = inputs.config_n32_int(0, sparse=sparse)
+        key = "n32_int32_sparse" if sparse else "n32_int32"
+        t0 = time.perf_counter()
+        oracle.blocked_topk(Q, 8)
+        out[key + "_blocked_s"] = time.perf_counter() - t0
+        wins = random_windows(32, 22, 4, 2)
+        t0 = time.perf_counter()
+        for lo, hi in wins:
+            oracle.brute_min(Q, lo, hi)
+        rate = len(wins) * 2.0 ** 22 / (time.perf_counter() - t0)
+        out[key + "_literal_states_per_s"] = rate
+        out[key + "_literal_s_extrapolated"] = 2.0 ** 32 / rate
+    # log Z: the oracle evaluates Eq. 1 for every state once for the minimum and
+    # once per beta; its rate on random windows of one n = 28 instance gives a
+    # lower bound for the 64-instance, 3-beta forward pass (exp not counted)
+    QL = inputs.config_logz(count=1)[0]
+    wins = random_windows(28, 22, 4, 3)
+    t0 = time.perf_counter()
+    for lo, hi in wins:
+        oracle.brute_min(QL, lo, hi)
+    rate = len(wins) * 2.0 ** 22 / (time.perf_counter() - t0)
+    out["logz_n28_literal_states_per_s"] = rate
+    out["logz_64x28_3beta_forward_s_lower_bound"] = 64 * 2.0 ** 28 * (1 + 3) / rate
+    Q40 = inputs.config_n40_f32(0)
+    lo = 0b100101 << 34
+    t0 = time.perf_counter()
+    oracle.blocked_min(Q40, lo, lo + (1 << 34))
+    dt = time.perf_counter() - t0
+    out["n40_blocked_states_per_s"] = 2.0 ** 34 / dt
+    out["n40_blocked_s_extrapolated"] = 2.0 ** 40 * dt / 2.0 ** 34
+    return out
 
 
 def init_ranks(world):
@@ -170,12 +282,12 @@ def run_reference(args, rank):
 
     Q = inputs.config_n40_f32(0)
     per_step = max(2.0, 60.0 / max(1, args.steps + args.warmup))
-    for _ in range(args.warmup):
-        cpu_baseline(Q, target_s=per_step / 4)
+    for w in range(args.warmup):
+        cpu_baseline(Q, target_s=per_step / 4, seed=100 + w)
     vals = []
     last = None
-    for _ in range(args.steps):
-        last = cpu_baseline(Q, target_s=per_step)
+    for st in range(args.steps):
+        last = cpu_baseline(Q, target_s=per_step, seed=st)
         vals.append(last["value"])
     v = statistics.median(vals)
     ms = (1 << N_VARS) / v * 1e3
@@ -185,7 +297,8 @@ def run_reference(args, rank):
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
         "data": "synthetic", "config": {"workload": WORKLOAD, "n": N_VARS},
         "cpu_baseline": {"value": v, "unit": "states/s", "cores": last["cores"],
-                         "kind": "oracle", "sample": last["sample"]},
+                         "kind": "oracle", "cpu_model": last["cpu_model"],
+                         "sample": last["sample"]},
         "e2e": {"value": v, "unit": "states/s", "h2d_bytes_per_step": 0,
                 "d2h_bytes_per_step": 0},
     }), flush=True)
@@ -316,14 +429,30 @@ def run_variants(dev, flush):
             ts.append(e0.elapsed_time(e1) * 1e-3)
         return statistics.median(ts)
 
-    # batched: 4096 instances, n ~ U{16..34}, half FP32 uniform[-1,1], half int16
+    # batched: 4096 instances, n ~ U{16..34}, half FP32 uniform[-1,1], half int16;
+    # timed with the library defaults, then again after qbf_tune has chosen the
+    # suffix width and CTAs per SM for every n of both element classes
     Qs = [torch.from_numpy(np.ascontiguousarray(q)).to(dev) for q in inputs.config_batched()]
     states = float(sum(2 ** q.shape[0] for q in Qs))
+    t_default = timed(lambda: qb.solve_batched(Qs))
+    cache = os.path.join(tempfile.mkdtemp(), "qbf_tune.txt")
+    t0 = time.perf_counter()
+    qb.qbf_tune(16, 34, qb.QBF_F32, cache)
+    qb.qbf_tune(16, 34, qb.QBF_I16, cache)
+    t_tune = time.perf_counter() - t0
     t = timed(lambda: qb.solve_batched(Qs))
+    tuned = {cls: {n: list(qb.qbf_tuned_params(n, code)) for n in range(16, 35)}
+             for cls, code in (("f32", qb.QBF_F32), ("i16", qb.QBF_I16))}
+    _, _, info = qb.solve_batched_info(Qs)
     out["batched_4096"] = {"workload": "4096 QUBOs, n ~ U{16..34}, half FP32 uniform[-1,1], "
                                        "half int16 uniform{-50..50}, seed 0; one persistent walk "
                                        "under a CUDA graph",
-                           "states": states, "seconds": t, "states_per_s": states / t}
+                           "states": states, "seconds": t, "states_per_s": states / t,
+                           "default_seconds": t_default,
+                           "tuned": {"by": "qbf_tune(16, 34) per element class",
+                                     "seconds_to_tune": t_tune,
+                                     "suffix_bits_ctas_per_sm_by_n": tuned},
+                           "n_candidates": int(sum(x.n_candidates for x in info))}
     # log Z forward and backward: 64 instances, n = 28, N(0, 1/n), beta in {0.1, 1, 10}
     QL = torch.from_numpy(inputs.config_logz()).to(dev)
     betas = list(inputs.LOGZ_BETAS)
@@ -391,6 +520,22 @@ def run_variants(dev, flush):
     t = timed(lambda: qb.solve(Q32))
     out["n32_int32"] = {"workload": "n=32 int32 uniform[-100,100], seed 0, exact",
                         "seconds": t, "states_per_s": 2.0 ** 32 / t}
+    # the same with each off-diagonal entry zeroed with p = 0.5: the split walk's
+    # per-state work does not read Q, so density should not change the time
+    Q32s = torch.from_numpy(inputs.config_n32_int(0, sparse=True)).to(dev)
+    walk = []
+
+    def sparse_one():
+        walk.append(qb.solve(Q32s, timing=True).walk_seconds)
+
+    t = timed(sparse_one)
+    dense_walk = []
+    timed(lambda: dense_walk.append(qb.solve(Q32, timing=True).walk_seconds))
+    out["n32_int32_sparse"] = {"workload": "n=32 int32 uniform[-100,100], seed 0, off-diagonal "
+                                           "zeroed with p=0.5 (mask seed 1), exact",
+                               "seconds": t, "states_per_s": 2.0 ** 32 / t,
+                               "min_kernel_ms": statistics.median(walk[1:]) * 1e3,
+                               "dense_min_kernel_ms": statistics.median(dense_walk[1:]) * 1e3}
     # n = 20 FP64 top-8 (latency)
     Q20 = torch.from_numpy(inputs.config_n20_f64(0)).to(dev)
     t = timed(lambda: qb.solve(Q20, top_k=8), reps=10)
@@ -567,6 +712,8 @@ def main():
         line["variants"] = run_variants(dev, flush)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(Qnp)
+        line["cpu_gray"] = cpu_gray_baseline(Qnp)
+        line["oracle_timings"] = oracle_timings()
     if rank == 0:
         print(json.dumps(line), flush=True)
     if pg:

@@ -108,7 +108,8 @@ typedef struct {
     int timing;         /* 1: time the main walk kernel with CUDA events on
                            `stream` and report it in qbf_result.walk_seconds */
     int batch_suffix_bits; /* qbf_solve_batched: suffix bits walked per lane,
-                              6..18; 0 = the autotuned value (default 16)  */
+                              6..18; 0 = the value qbf_tune chose for the
+                              instance's n (cache), else 16                 */
     int reserved[6];
 } qbf_options;
 
@@ -267,7 +268,8 @@ int qubo_bf_solve(const void *Q_host, int n, int dtype, double *min_value, uint6
  *             elements of dtype[i], row-major.
  * n, dtype  : host arrays of `count` entries; 1 <= n[i] <= QBF_BATCH_MAX_N.
  * opt       : NULL or top_k = 1, fix_bits = 0; batch_suffix_bits selects the
- *             per-lane suffix width (0 = autotuned, see qbf_tune_batched);
+ *             per-lane suffix width (0 = the qbf_tune choice for each
+ *             instance's n, else 16; see qbf_tune and qbf_tune_batched);
  *             variant AUTO / SPLIT_DEFER (instances whose image fits 2^23
  *             walk in the deferred-correction form, the rest in int32; AUTO
  *             repeats the batch on the int32 walk after QBF_EOVERFLOW),
@@ -281,6 +283,64 @@ int qubo_bf_solve(const void *Q_host, int n, int dtype, double *min_value, uint6
  */
 int qbf_solve_batched(const void *const *Q_dev, const int *n, const int *dtype, int count,
                       const qbf_options *opt, double *min_value, uint64_t *argmin, void *stream);
+
+/*
+ * qbf_solve_batched_info -- qbf_solve_batched with per-instance certification
+ * details.
+ *
+ * Same arguments, work and status codes as qbf_solve_batched (the result
+ * struct of the paper's listing, per instance: the minimum and its vector,
+ * Appendix A), plus `info`: NULL or a host array of `count` entries.  Entry i
+ * describes how instance i was certified:
+ */
+typedef struct {
+    double error_bound;    /* half-width of the certification window in units
+                              of f (0 for integer Q), as qbf_result         */
+    uint64_t n_candidates; /* states rescored for this instance            */
+    int scale_bits;        /* sigma of the instance's fixed-point image     */
+    int suffix_bits;       /* suffix bits walked per lane (n - prefix bits)  */
+    int prefix_bits;       /* prefix bits (2^prefix_bits prefixes)          */
+    int walk;              /* MIN walk the instance took: QBF_VARIANT_SPLIT_DEFER,
+                              QBF_VARIANT_SPLIT_MIX or QBF_VARIANT_SPLIT    */
+} qbf_batch_info;
+/* Per-instance top-k is not offered (top_k > 1 gives QBF_ENOTIMPL): a
+ * batched caller wanting the k best of one instance calls qbf_solve on it. */
+int qbf_solve_batched_info(const void *const *Q_dev, const int *n, const int *dtype, int count,
+                           const qbf_options *opt, double *min_value, uint64_t *argmin,
+                           qbf_batch_info *info, void *stream);
+
+/*
+ * qbf_tune -- autotuner of the batched solver, per n and element class.
+ *
+ * For every n in [n_min, n_max] (1 <= n_min <= n_max <= QBF_BATCH_MAX_N) it
+ * builds a synthetic batch of that n on the current device (upper-triangular
+ * instances, uniform in [-1, 1] for float dtypes, integers in [-50, 50] for
+ * integer dtypes; about 2^37 states, at most 4096 instances), times
+ * qbf_solve_batched over the suffix width walked per lane (which fixes the
+ * prefix width k = n - suffix bits, Section 3.1's split) and the number of
+ * resident 128-thread CTAs per SM of the walk kernel, and keeps the fastest
+ * pair (suffix width first, then CTAs per SM at that width).  The choices
+ * take effect at once in this process for the current device, and one line
+ * per n is appended to `cache_path`:
+ *     qbf-tune-v1 <device name> <SM count> <class> <n> <suffix bits> <CTAs/SM> <seconds>
+ * (class 0 = float, 1 = integer; spaces in the name become '_').  NULL uses the
+ * default cache: the file named by the environment variable QBF_TUNE_CACHE,
+ * else $HOME/.cache/qbf_tune.txt.  qbf_solve_batched reads the default cache
+ * once per device on its first call (later lines win) and uses, for each
+ * instance, the tuned suffix width of its n and class, and for the walk grid
+ * the CTAs per SM of the n that holds the most states of the batch; an
+ * explicit batch_suffix_bits in the options overrides the suffix width.
+ * Allocates its synthetic batch with cudaMalloc and frees it; synchronises the
+ * device.  Errors: QBF_EINVAL (range, dtype), QBF_ECUDA, and QBF_EINVAL when
+ * the cache file cannot be written (the in-process choices are kept).
+ */
+int qbf_tune(int n_min, int n_max, int dtype, const char *cache_path);
+
+/* The batched solver's current choices for instances of n variables and
+ * `dtype` on the current device (after qbf_tune or a loaded cache): suffix
+ * bits walked per lane and CTAs per SM, 0 where nothing is tuned (then the
+ * defaults apply: 16 suffix bits, as many CTAs as fit). */
+int qbf_tuned_params(int n, int dtype, int *suffix_bits, int *ctas_per_sm);
 
 /*
  * qbf_tune_batched -- picks the per-lane suffix width of qbf_solve_batched.

@@ -65,6 +65,17 @@ class QbfResult(ctypes.Structure):
     ]
 
 
+class QbfBatchInfo(ctypes.Structure):
+    _fields_ = [
+        ("error_bound", ctypes.c_double),
+        ("n_candidates", ctypes.c_uint64),
+        ("scale_bits", ctypes.c_int),
+        ("suffix_bits", ctypes.c_int),
+        ("prefix_bits", ctypes.c_int),
+        ("walk", ctypes.c_int),
+    ]
+
+
 QBF_CKPT_VERSION = 1
 
 
@@ -123,6 +134,16 @@ _SIGS = {
                                          ctypes.POINTER(ctypes.c_int), ctypes.c_int,
                                          ctypes.POINTER(QbfOptions), ctypes.POINTER(ctypes.c_double),
                                          ctypes.POINTER(ctypes.c_uint64), _VP]),
+    "qbf_solve_batched_info": (ctypes.c_int, [ctypes.POINTER(ctypes.c_void_p),
+                                              ctypes.POINTER(ctypes.c_int),
+                                              ctypes.POINTER(ctypes.c_int), ctypes.c_int,
+                                              ctypes.POINTER(QbfOptions),
+                                              ctypes.POINTER(ctypes.c_double),
+                                              ctypes.POINTER(ctypes.c_uint64),
+                                              ctypes.POINTER(QbfBatchInfo), _VP]),
+    "qbf_tune": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_char_p]),
+    "qbf_tuned_params": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.POINTER(ctypes.c_int),
+                                        ctypes.POINTER(ctypes.c_int)]),
     "qbf_tune_batched": (ctypes.c_int, [ctypes.POINTER(ctypes.c_void_p), ctypes.POINTER(ctypes.c_int),
                                         ctypes.POINTER(ctypes.c_int), ctypes.c_int, ctypes.c_int,
                                         ctypes.c_int, ctypes.POINTER(ctypes.c_int),
@@ -277,6 +298,33 @@ def qbf_solve_batched(Q_ptrs, ns, dtypes, opt: QbfOptions | None, stream: int | 
     return list(vmin), [int(v) for v in am]
 
 
+def qbf_solve_batched_info(Q_ptrs, ns, dtypes, opt: QbfOptions | None,
+                           stream: int | None = None):
+    """As qbf_solve_batched, plus one QbfBatchInfo per instance."""
+    count, P, N, D = _batch_arrays(Q_ptrs, ns, dtypes)
+    vmin = (ctypes.c_double * count)()
+    am = (ctypes.c_uint64 * count)()
+    info = (QbfBatchInfo * count)()
+    rc = lib().qbf_solve_batched_info(P, N, D, count,
+                                      ctypes.byref(opt) if opt is not None else None, vmin, am,
+                                      info, _VP(stream or 0))
+    _check(rc)
+    return list(vmin), [int(v) for v in am], list(info)
+
+
+def qbf_tune(n_min: int, n_max: int, dtype: int, cache_path: str | None = None) -> None:
+    """Tune the batched solver per n (suffix width, CTAs per SM); see include/qbf.h."""
+    _check(lib().qbf_tune(n_min, n_max, dtype,
+                          cache_path.encode() if cache_path is not None else None))
+
+
+def qbf_tuned_params(n: int, dtype: int):
+    """(suffix bits, CTAs per SM) the batched solver uses for n and dtype; 0 = default."""
+    ns, ctas = ctypes.c_int(), ctypes.c_int()
+    _check(lib().qbf_tuned_params(n, dtype, ctypes.byref(ns), ctypes.byref(ctas)))
+    return ns.value, ctas.value
+
+
 def qbf_tune_batched(Q_ptrs, ns, dtypes, lo_bits: int = 6, hi_bits: int = 16,
                      stream: int | None = None):
     count, P, N, D = _batch_arrays(Q_ptrs, ns, dtypes)
@@ -286,6 +334,20 @@ def qbf_tune_batched(Q_ptrs, ns, dtypes, lo_bits: int = 6, hi_bits: int = 16,
                                 ctypes.byref(sec), _VP(stream or 0))
     _check(rc)
     return best.value, sec.value
+
+
+def solve_batched_info(Qs, batch_suffix_bits: int = 0, stream=None,
+                       variant: int = QBF_VARIANT_AUTO):
+    """Like solve_batched; returns (min_values, argmins, per-instance QbfBatchInfo)."""
+    import torch
+
+    Qs = [q.contiguous() for q in Qs]
+    opt = qbf_default_options()
+    opt.batch_suffix_bits = batch_suffix_bits
+    opt.variant = variant
+    s = stream if stream is not None else torch.cuda.current_stream().cuda_stream
+    return qbf_solve_batched_info([q.data_ptr() for q in Qs], [q.shape[0] for q in Qs],
+                                  [dtype_code(q) for q in Qs], opt, s)
 
 
 def solve_batched(Qs, batch_suffix_bits: int = 0, stream=None, variant: int = QBF_VARIANT_AUTO):

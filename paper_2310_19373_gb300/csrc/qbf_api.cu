@@ -985,6 +985,24 @@ int qbf_solve_batched(const void *const *Q_dev, const int *n, const int *dtype, 
                          nullptr);
 }
 
+int qbf_solve_batched_info(const void *const *Q_dev, const int *n, const int *dtype, int count,
+                           const qbf_options *opt, double *min_value, uint64_t *argmin,
+                           qbf_batch_info *info, void *stream)
+{
+    return solve_batched(Q_dev, n, dtype, count, opt, min_value, argmin, (cudaStream_t)stream,
+                         nullptr, info, 0);
+}
+
+int qbf_tune(int n_min, int n_max, int dtype, const char *cache_path)
+{
+    return tune_batched_table(n_min, n_max, dtype, cache_path);
+}
+
+int qbf_tuned_params(int n, int dtype, int *suffix_bits, int *ctas_per_sm)
+{
+    return tuned_params(n, dtype, suffix_bits, ctas_per_sm);
+}
+
 int qbf_tune_batched(const void *const *Q_dev, const int *n, const int *dtype, int count,
                      int lo_bits, int hi_bits, int *best_bits, double *best_seconds, void *stream)
 {

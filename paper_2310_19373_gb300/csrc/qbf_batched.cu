@@ -27,6 +27,8 @@
 
 #include <algorithm>
 #include <climits>
+#include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <mutex>
 #include <string>
@@ -55,6 +57,14 @@ constexpr int kWarpSmemInts =
     (512 + QBF_BATCH_MAX_N * QBF_BATCH_MAX_N + QBF_BATCH_MAX_N + 128 +
      2 * (kBatchMaxNS - kBatchR) * 32 + 3) & ~3;
 constexpr unsigned long long kBatchCandCap = 1ull << 20;
+
+// per-instance certification details, filled on the device (qbf_batch_info)
+struct BatchInfoDev {
+    double error_bound;
+    unsigned long long ncand;
+    int sigma;
+    int walk;
+};
 
 struct BatchArgs {
     const BatchDesc *desc;
@@ -241,10 +251,12 @@ __global__ void __launch_bounds__(kBatchThreads) batched_walk_kernel(BatchArgs a
 }
 
 __global__ void batched_reset_kernel(int count, int *gmin, unsigned long long *best_key,
-                                     unsigned long long *best_idx, unsigned *lowest, Counters *ctr)
+                                     unsigned long long *best_idx, unsigned *lowest, Counters *ctr,
+                                     BatchInfoDev *info)
 {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i < count) {
+        info[i].ncand = 0;
         gmin[i] = INT_MAX;
         lowest[i] = 0xFFFFFFFFu;
         best_key[i] = ~0ull;
@@ -323,7 +335,7 @@ __device__ __forceinline__ double q_at_b(const void *Q, int dtype, int e)
 __global__ void batched_rescore_kernel(const BatchDesc *desc, const unsigned long long *cand_idx,
                                        const unsigned *cand_inst, const Counters *ctr,
                                        unsigned long long cap, unsigned long long *keys,
-                                       unsigned long long *best_key)
+                                       unsigned long long *best_key, BatchInfoDev *info)
 {
     const unsigned long long count = ctr->cand < cap ? ctr->cand : cap;
     for (unsigned long long e = blockIdx.x * (unsigned long long)blockDim.x + threadIdx.x;
@@ -362,7 +374,26 @@ __global__ void batched_rescore_kernel(const BatchDesc *desc, const unsigned lon
         }
         keys[e] = key;
         atomicMin(&best_key[inst], key);
+        atomicAdd(&info[inst].ncand, 1ull);
     }
+}
+
+// sigma, window and MIN walk form of every instance (the walk choice repeats
+// the MIN kernel's eligibility test)
+__global__ void batched_info_kernel(const BatchDesc *desc, int count, const Plan *plans, int mix,
+                                    BatchInfoDev *info)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= count)
+        return;
+    const Plan *plan = plans + i;
+    const bool is_int = (desc[i].dtype == QBF_I32 || desc[i].dtype == QBF_I16);
+    info[i].sigma = plan->sigma;
+    info[i].error_bound = is_int ? 0.0 : plan->error_bound;
+    const bool eight = mix && plan->status == QBF_OK && desc[i].ns >= kBatchR + 3 &&
+                       plan->vhat <= (long long)kF32Vmax;
+    info[i].walk = eight ? (mix == 2 ? QBF_VARIANT_SPLIT_DEFER : QBF_VARIANT_SPLIT_MIX)
+                         : QBF_VARIANT_SPLIT;
 }
 
 __global__ void batched_argmin_kernel(const unsigned long long *cand_idx,
@@ -385,7 +416,7 @@ __global__ void batched_argmin_kernel(const unsigned long long *cand_idx,
 
 struct BLayout {
     size_t desc, plans, K, recs, item_min, flagged, gmin, best_key, best_idx, status, lowest,
-        ctr, cand_idx, cand_inst, keys, total;
+        ctr, cand_idx, cand_inst, keys, info, total;
 };
 
 size_t a256(size_t x) { return (x + 255) & ~(size_t)255; }
@@ -414,13 +445,14 @@ BLayout blayout(int count, unsigned long long nrec, unsigned long long items)
     L.cand_idx = take(sizeof(unsigned long long) * kBatchCandCap);
     L.cand_inst = take(sizeof(unsigned) * kBatchCandCap);
     L.keys = take(sizeof(unsigned long long) * kBatchCandCap);
+    L.info = take(sizeof(BatchInfoDev) * count);
     L.total = o;
     return L;
 }
 
 // host staging (pinned): descriptors in, results out
 struct BStage {
-    size_t desc, best_key, best_idx, status, ctr, total;
+    size_t desc, best_key, best_idx, status, ctr, info, total;
 };
 
 BStage bstage(int count)
@@ -437,6 +469,7 @@ BStage bstage(int count)
     S.best_idx = take(sizeof(unsigned long long) * count);
     S.status = take(sizeof(int) * count);
     S.ctr = take(sizeof(Counters));
+    S.info = take(sizeof(BatchInfoDev) * count);
     S.total = o;
     return S;
 }
@@ -461,6 +494,10 @@ struct BatchState {
     GraphKey key;
     bool have_key = false;
     int tuned_ns = 0;
+    // qbf_tune's choices per element class (0 float, 1 integer) and n; 0 = none
+    int tab_ns[2][QBF_BATCH_MAX_N + 1] = {};
+    int tab_ctas[2][QBF_BATCH_MAX_N + 1] = {};
+    bool cache_loaded = false;
 };
 
 std::mutex g_bmu;
@@ -477,6 +514,63 @@ int walk_bps(int mode)
         e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, batched_walk_kernel<kModeEmit>,
                                                           kBatchThreads, 0);
     return (e != cudaSuccess || b < 1) ? 1 : b;
+}
+
+std::string default_tune_cache()
+{
+    if (const char *p = getenv("QBF_TUNE_CACHE"))
+        if (*p)
+            return p;
+    if (const char *h = getenv("HOME"))
+        if (*h)
+            return std::string(h) + "/.cache/qbf_tune.txt";
+    return std::string();
+}
+
+// device name with spaces replaced by '_' and its SM count
+void device_tag(int dev, std::string *name, int *nsm)
+{
+    cudaDeviceProp prop;
+    memset(&prop, 0, sizeof(prop));
+    cudaGetDeviceProperties(&prop, dev);
+    for (char *c = prop.name; *c; ++c)
+        if (*c == ' ')
+            *c = '_';
+    *name = prop.name;
+    *nsm = prop.multiProcessorCount;
+}
+
+// Read the lines of the default tuning cache that match this device; later
+// lines win.  A missing or unreadable file leaves the tables empty.
+void load_tune_cache(BatchState &B, int dev)
+{
+    B.cache_loaded = true;
+    const std::string path = default_tune_cache();
+    if (path.empty())
+        return;
+    FILE *f = fopen(path.c_str(), "r");
+    if (!f)
+        return;
+    std::string name;
+    int nsm = 0;
+    device_tag(dev, &name, &nsm);
+    char tag[32], dname[256];
+    int fnsm, cls, n, ns, ctas;
+    double sec;
+    char line[512];
+    while (fgets(line, sizeof(line), f)) {
+        if (sscanf(line, "%31s %255s %d %d %d %d %d %lf", tag, dname, &fnsm, &cls, &n, &ns, &ctas,
+                   &sec) != 8)
+            continue;
+        if (strcmp(tag, "qbf-tune-v1") != 0 || name != dname || fnsm != nsm)
+            continue;
+        if (cls < 0 || cls > 1 || n < 1 || n > QBF_BATCH_MAX_N || ns < kBatchR ||
+            ns > kBatchMaxNS || ctas < 1 || ctas > 64)
+            continue;
+        B.tab_ns[cls][n] = ns;
+        B.tab_ctas[cls][n] = ctas;
+    }
+    fclose(f);
 }
 
 #define B_CUDA(call, where)                                                                      \
@@ -504,8 +598,9 @@ int enqueue_batch(BatchState &B, const BLayout &L, const BStage &S, int count,
                            cudaMemcpyHostToDevice, s),
            "batch descriptors");
     unsigned *lowest = (unsigned *)(d + L.lowest);
+    BatchInfoDev *info = (BatchInfoDev *)(d + L.info);
     batched_reset_kernel<<<(count + 255) / 256, 256, 0, s>>>(count, gmin, best_key, best_idx,
-                                                             lowest, ctr);
+                                                             lowest, ctr, info);
     batched_prepare_kernel<<<count, 256, 0, s>>>(desc, plans, (int *)(d + L.status),
                                                  mix ? kF32Vmax : (long long)INT_MAX);
     batched_tables_kernel<<<count, 256, 0, s>>>(desc, plans, recs, K);
@@ -534,7 +629,8 @@ int enqueue_batch(BatchState &B, const BLayout &L, const BStage &S, int count,
     batched_walk_kernel<kModeEmit><<<grid_emit, kBatchThreads, 0, s>>>(a);
     unsigned long long *keys = (unsigned long long *)(d + L.keys);
     batched_rescore_kernel<<<512, 256, 0, s>>>(desc, a.cand_idx, a.cand_inst, ctr, kBatchCandCap,
-                                               keys, best_key);
+                                               keys, best_key, info);
+    batched_info_kernel<<<(count + 255) / 256, 256, 0, s>>>(desc, count, plans, mix, info);
     batched_argmin_kernel<<<512, 256, 0, s>>>(a.cand_idx, a.cand_inst, ctr, kBatchCandCap, keys,
                                               best_key, best_idx);
     B_CUDA(cudaGetLastError(), "batched kernels");
@@ -549,6 +645,9 @@ int enqueue_batch(BatchState &B, const BLayout &L, const BStage &S, int count,
            "batch status");
     B_CUDA(cudaMemcpyAsync(h + S.ctr, ctr, sizeof(Counters), cudaMemcpyDeviceToHost, s),
            "batch counters");
+    B_CUDA(cudaMemcpyAsync(h + S.info, info, sizeof(BatchInfoDev) * count, cudaMemcpyDeviceToHost,
+                           s),
+           "batch info");
     return QBF_OK;
 }
 
@@ -564,7 +663,8 @@ int dtsize(int dt)
 // deferred-correction (2) MIN walk; mix = 0: the int32 walk throughout.
 int solve_batched_mode(const void *const *Q, const int *n, const int *dtype, int count,
                        const qbf_options *opt_in, double *min_value, uint64_t *argmin,
-                       cudaStream_t s, int *kernel_launches, int mix)
+                       cudaStream_t s, int *kernel_launches, int mix, qbf_batch_info *info_out,
+                       int ctas_override)
 {
     if (!Q || !n || !dtype || !min_value || !argmin)
         return record_error(QBF_EINVAL, "null pointer argument");
@@ -584,9 +684,14 @@ int solve_batched_mode(const void *const *Q, const int *n, const int *dtype, int
     if ((int)g_bstate.size() <= dev)
         g_bstate.resize(dev + 1);
     BatchState &B = g_bstate[dev];
-    int NS = o.batch_suffix_bits > 0 ? o.batch_suffix_bits : (B.tuned_ns > 0 ? B.tuned_ns : 16);
-    if (NS < kBatchR || NS > kBatchMaxNS)
+    if (!B.cache_loaded)
+        load_tune_cache(B, dev);
+    if (o.batch_suffix_bits != 0 &&
+        (o.batch_suffix_bits < kBatchR || o.batch_suffix_bits > kBatchMaxNS))
         return record_error(QBF_EINVAL, "batch_suffix_bits must be in [6, 18]");
+    const int NS_default = B.tuned_ns > 0 ? B.tuned_ns : 16;
+    // states per (class, n): the n holding the most states picks the CTAs per SM
+    double states_cn[2][QBF_BATCH_MAX_N + 1] = {};
 
     // plan every instance
     std::vector<BatchDesc> desc(count);
@@ -605,6 +710,11 @@ int solve_batched_mode(const void *const *Q, const int *n, const int *dtype, int
         d.n_src = n[i];
         d.n = std::max(n[i], kBatchMinN);
         d.dtype = dtype[i];
+        const int cls = (dtype[i] == QBF_I32 || dtype[i] == QBF_I16) ? 1 : 0;
+        const int NS = o.batch_suffix_bits > 0
+                           ? o.batch_suffix_bits
+                           : (B.tab_ns[cls][n[i]] > 0 ? B.tab_ns[cls][n[i]] : NS_default);
+        states_cn[cls][n[i]] += (double)(1ull << n[i]);
         d.ns = std::max(kBatchR, std::min(NS, d.n - 5));
         d.nprefix = 1ull << (d.n - d.ns);
         d.item_off = items;
@@ -641,8 +751,21 @@ int solve_batched_mode(const void *const *Q, const int *n, const int *dtype, int
 
     int nsm = 1;
     cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+    int ctas = ctas_override;
+    if (ctas <= 0) {
+        int bc = 0, bn = 1;
+        for (int c = 0; c < 2; ++c)
+            for (int m = 1; m <= QBF_BATCH_MAX_N; ++m)
+                if (states_cn[c][m] > states_cn[bc][bn]) {
+                    bc = c;
+                    bn = m;
+                }
+        ctas = B.tab_ctas[bc][bn];
+    }
+    const int bps = walk_bps(kModeMin);
+    const int cps = (ctas > 0 && ctas < bps) ? ctas : bps;
     const int grid_min = (int)std::max<unsigned long long>(
-        1, std::min<unsigned long long>((unsigned long long)nsm * walk_bps(kModeMin),
+        1, std::min<unsigned long long>((unsigned long long)nsm * cps,
                                         (items + kBatchWarps - 1) / kBatchWarps));
     const int grid_emit = nsm * walk_bps(kModeEmit);
 
@@ -683,7 +806,7 @@ int solve_batched_mode(const void *const *Q, const int *n, const int *dtype, int
     B_CUDA(cudaGraphLaunch(B.exec, s), "graph launch");
     B_CUDA(cudaStreamSynchronize(s), "batched solve");
     if (kernel_launches)
-        *kernel_launches = 10;
+        *kernel_launches = 11;
 
     const unsigned long long *bk = (const unsigned long long *)(h + S.best_key);
     const unsigned long long *bi = (const unsigned long long *)(h + S.best_idx);
@@ -714,6 +837,17 @@ int solve_batched_mode(const void *const *Q, const int *n, const int *dtype, int
         }
         argmin[i] = bi[i];
     }
+    if (info_out) {
+        const BatchInfoDev *inf = (const BatchInfoDev *)(h + S.info);
+        for (int i = 0; i < count; ++i) {
+            info_out[i].error_bound = inf[i].error_bound;
+            info_out[i].n_candidates = inf[i].ncand;
+            info_out[i].scale_bits = inf[i].sigma;
+            info_out[i].suffix_bits = desc[i].ns;
+            info_out[i].prefix_bits = desc[i].n - desc[i].ns;
+            info_out[i].walk = inf[i].walk;
+        }
+    }
     return QBF_OK;
 }
 
@@ -723,7 +857,7 @@ int solve_batched_mode(const void *const *Q, const int *n, const int *dtype, int
 // QBF_VARIANT_SPLIT: the int32 pass.
 int solve_batched(const void *const *Q, const int *n, const int *dtype, int count,
                   const qbf_options *opt_in, double *min_value, uint64_t *argmin,
-                  cudaStream_t s, int *kernel_launches)
+                  cudaStream_t s, int *kernel_launches, qbf_batch_info *info, int ctas_override)
 {
     const int variant = opt_in ? opt_in->variant : QBF_VARIANT_AUTO;
     if (variant != QBF_VARIANT_AUTO && variant != QBF_VARIANT_SPLIT &&
@@ -732,13 +866,13 @@ int solve_batched(const void *const *Q, const int *n, const int *dtype, int coun
                             "qbf_solve_batched runs the int32, two-pipe or deferred-correction walk");
     if (variant == QBF_VARIANT_SPLIT)
         return solve_batched_mode(Q, n, dtype, count, opt_in, min_value, argmin, s,
-                                  kernel_launches, 0);
+                                  kernel_launches, 0, info, ctas_override);
     const int rc = solve_batched_mode(Q, n, dtype, count, opt_in, min_value, argmin, s,
-                                      kernel_launches,
-                                      variant == QBF_VARIANT_SPLIT_MIX ? 1 : 2);
+                                      kernel_launches, variant == QBF_VARIANT_SPLIT_MIX ? 1 : 2,
+                                      info, ctas_override);
     if (rc == QBF_EOVERFLOW && variant == QBF_VARIANT_AUTO)
         return solve_batched_mode(Q, n, dtype, count, opt_in, min_value, argmin, s,
-                                  kernel_launches, 0);
+                                  kernel_launches, 0, info, ctas_override);
     return rc;
 }
 
@@ -773,11 +907,205 @@ int release_batched()
             cudaFree(B.dev);
         if (B.host)
             cudaFreeHost(B.host);
-        const int keep = B.tuned_ns;
-        B = BatchState();
-        B.tuned_ns = keep;
+        BatchState keep = BatchState();
+        keep.tuned_ns = B.tuned_ns;
+        memcpy(keep.tab_ns, B.tab_ns, sizeof(B.tab_ns));
+        memcpy(keep.tab_ctas, B.tab_ctas, sizeof(B.tab_ctas));
+        keep.cache_loaded = B.cache_loaded;
+        B = keep;
     }
     cudaSetDevice(cur);
+    return QBF_OK;
+}
+
+
+namespace {
+
+// Synthetic tuning instances: upper triangular, entries from a counter hash
+// (splitmix64 finaliser) -- uniform in [-1, 1] for float dtypes, integers in
+// [-50, 50] for integer dtypes.  Only the timing depends on them.
+__global__ void tune_fill_kernel(void *buf, int n, int dtype, unsigned long long total,
+                                 unsigned long long seed)
+{
+    for (unsigned long long e = blockIdx.x * (unsigned long long)blockDim.x + threadIdx.x;
+         e < total; e += (unsigned long long)gridDim.x * blockDim.x) {
+        const unsigned long long w = e % ((unsigned long long)n * n);
+        const int i = (int)(w / n), j = (int)(w % n);
+        unsigned long long z = seed + e * 0x9E3779B97F4A7C15ull;
+        z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+        z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+        z ^= z >> 31;
+        const bool keep = (j >= i);
+        const double u = (double)(z >> 11) * (1.0 / 9007199254740992.0);  // [0, 1)
+        const int iv = keep ? (int)(z % 101ull) - 50 : 0;
+        const double fv = keep ? 2.0 * u - 1.0 : 0.0;
+        switch (dtype) {
+        case QBF_F64: static_cast<double *>(buf)[e] = fv; break;
+        case QBF_F32: static_cast<float *>(buf)[e] = (float)fv; break;
+        case QBF_I32: static_cast<int *>(buf)[e] = iv; break;
+        default: static_cast<short *>(buf)[e] = (short)iv; break;
+        }
+    }
+}
+
+}  // namespace
+
+// One n of qbf_tune: time the batch for every suffix width at the largest CTA
+// count, then every CTA count at the best width; returns QBF_OK and the choice.
+static int tune_one_n(int n, int dtype, cudaStream_t s, int *best_ns, int *best_ctas,
+                      double *best_sec)
+{
+    const int esz = dtsize(dtype);
+    // about 2^37 states (at most 4096 instances): the work queue then runs many
+    // waves, as in a large mixed batch, so the choice reflects the steady
+    // state and not the tail of one small launch
+    const unsigned long long count =
+        std::max<unsigned long long>(1, std::min<unsigned long long>(4096, (1ull << 37) >> n));
+    const unsigned long long per = (unsigned long long)n * n;
+    void *buf = nullptr;
+    B_CUDA(cudaMalloc(&buf, per * count * esz), "cudaMalloc(tuning batch)");
+    tune_fill_kernel<<<256, 256, 0, s>>>(buf, n, dtype, per * count, 0x5EEDull + n);
+    cudaError_t fe = cudaStreamSynchronize(s);
+    if (fe != cudaSuccess) {
+        cudaFree(buf);
+        return record_error(QBF_ECUDA, "tuning batch fill");
+    }
+    std::vector<const void *> ptr(count);
+    std::vector<int> nn(count, n), dt(count, dtype);
+    for (unsigned long long i = 0; i < count; ++i)
+        ptr[i] = static_cast<const char *>(buf) + i * per * esz;
+    std::vector<double> vmin(count);
+    std::vector<uint64_t> am(count);
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    cudaEventCreate(&e0);
+    cudaEventCreate(&e1);
+    int rc = QBF_OK;
+    auto time_one = [&](int ns, int ctas, double *sec) -> int {
+        qbf_options o;
+        qbf_default_options(&o);
+        o.batch_suffix_bits = ns;
+        // first call builds the graph for this layout; then the median of three
+        int r = solve_batched(ptr.data(), nn.data(), dt.data(), (int)count, &o, vmin.data(),
+                              am.data(), s, nullptr, nullptr, ctas);
+        if (r)
+            return r;
+        float t[3];
+        for (int k = 0; k < 3; ++k) {
+            cudaEventRecord(e0, s);
+            r = solve_batched(ptr.data(), nn.data(), dt.data(), (int)count, &o, vmin.data(),
+                              am.data(), s, nullptr, nullptr, ctas);
+            cudaEventRecord(e1, s);
+            cudaEventSynchronize(e1);
+            if (r)
+                return r;
+            cudaEventElapsedTime(&t[k], e0, e1);
+        }
+        std::sort(t, t + 3);
+        *sec = t[1] * 1e-3;
+        return QBF_OK;
+    };
+    const int bps = walk_bps(kModeMin);
+    const int nw = std::max(n, kBatchMinN);
+    const int ns_hi = std::max(kBatchR, std::min(kBatchMaxNS, nw - 5));
+    double bsec = 1e300;
+    int bns = ns_hi, bct = bps;
+    for (int ns = kBatchR; ns <= ns_hi && rc == QBF_OK; ++ns) {
+        double t = 0;
+        rc = time_one(ns, bps, &t);
+        if (rc == QBF_OK && t < bsec) {
+            bsec = t;
+            bns = ns;
+        }
+    }
+    for (int c = 1; c < bps && rc == QBF_OK; ++c) {
+        double t = 0;
+        rc = time_one(bns, c, &t);
+        if (rc == QBF_OK && t < bsec) {
+            bsec = t;
+            bct = c;
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    cudaFree(buf);
+    if (rc)
+        return rc;
+    *best_ns = bns;
+    *best_ctas = bct;
+    *best_sec = bsec;
+    return QBF_OK;
+}
+
+int tune_batched_table(int n_min, int n_max, int dtype, const char *cache_path)
+{
+    if (n_min < 1 || n_max > QBF_BATCH_MAX_N || n_min > n_max)
+        return record_error(QBF_EINVAL, "qbf_tune: need 1 <= n_min <= n_max <= 34");
+    if (dtsize(dtype) == 0)
+        return record_error(QBF_EDTYPE, "qbf_tune: unknown dtype");
+    int dev = 0;
+    B_CUDA(cudaGetDevice(&dev), "cudaGetDevice");
+    {
+        std::lock_guard<std::mutex> lk(g_bmu);
+        if ((int)g_bstate.size() <= dev)
+            g_bstate.resize(dev + 1);
+        if (!g_bstate[dev].cache_loaded)
+            load_tune_cache(g_bstate[dev], dev);
+    }
+    cudaStream_t s = nullptr;
+    B_CUDA(cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking), "tuning stream");
+    const int cls = (dtype == QBF_I32 || dtype == QBF_I16) ? 1 : 0;
+    std::string name;
+    int nsm = 0;
+    device_tag(dev, &name, &nsm);
+    std::string lines;
+    int rc = QBF_OK;
+    for (int n = n_min; n <= n_max && rc == QBF_OK; ++n) {
+        int ns = 0, ctas = 0;
+        double sec = 0;
+        rc = tune_one_n(n, dtype, s, &ns, &ctas, &sec);
+        if (rc)
+            break;
+        {
+            std::lock_guard<std::mutex> lk(g_bmu);
+            g_bstate[dev].tab_ns[cls][n] = ns;
+            g_bstate[dev].tab_ctas[cls][n] = ctas;
+        }
+        char buf[512];
+        snprintf(buf, sizeof(buf), "qbf-tune-v1 %s %d %d %d %d %d %.9f\n", name.c_str(), nsm, cls,
+                 n, ns, ctas, sec);
+        lines += buf;
+    }
+    cudaStreamDestroy(s);
+    if (rc)
+        return rc;
+    const std::string path = cache_path ? std::string(cache_path) : default_tune_cache();
+    if (!path.empty()) {
+        FILE *f = fopen(path.c_str(), "a");
+        if (!f)
+            return record_error(QBF_EINVAL, ("qbf_tune: cannot write the cache " + path).c_str());
+        fputs(lines.c_str(), f);
+        fclose(f);
+    }
+    return QBF_OK;
+}
+
+int tuned_params(int n, int dtype, int *suffix_bits, int *ctas_per_sm)
+{
+    if (!suffix_bits || !ctas_per_sm)
+        return record_error(QBF_EINVAL, "null pointer argument");
+    if (n < 1 || n > QBF_BATCH_MAX_N || dtsize(dtype) == 0)
+        return record_error(QBF_EINVAL, "qbf_tuned_params: n in [1, 34] and a known dtype");
+    int dev = 0;
+    B_CUDA(cudaGetDevice(&dev), "cudaGetDevice");
+    std::lock_guard<std::mutex> lk(g_bmu);
+    if ((int)g_bstate.size() <= dev)
+        g_bstate.resize(dev + 1);
+    BatchState &B = g_bstate[dev];
+    if (!B.cache_loaded)
+        load_tune_cache(B, dev);
+    const int cls = (dtype == QBF_I32 || dtype == QBF_I16) ? 1 : 0;
+    *suffix_bits = B.tab_ns[cls][n];
+    *ctas_per_sm = B.tab_ctas[cls][n];
     return QBF_OK;
 }
 

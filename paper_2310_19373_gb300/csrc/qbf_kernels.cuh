@@ -68,8 +68,10 @@ int record_error(int code, const char *msg);
 // qbf_batched.cu
 int solve_batched(const void *const *Q, const int *n, const int *dtype, int count,
                   const qbf_options *opt, double *min_value, uint64_t *argmin, cudaStream_t s,
-                  int *kernel_launches);
+                  int *kernel_launches, qbf_batch_info *info = nullptr, int ctas_override = 0);
 int set_tuned_batch_ns(int ns);
+int tune_batched_table(int n_min, int n_max, int dtype, const char *cache_path);
+int tuned_params(int n, int dtype, int *suffix_bits, int *ctas_per_sm);
 int release_batched();
 
 // qbf_logz.cu

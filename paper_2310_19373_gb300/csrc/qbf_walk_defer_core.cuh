@@ -164,17 +164,22 @@ __device__ __forceinline__ int walk_min(Lane<R> &L, int n, int nsg, const int4 *
     if (M == 0) {
         block<R, 0>(L, cs);
     } else {
+        // records are read at the transition, not prefetched a block pair
+        // ahead: the 16 registers a prefetch holds keep the kernel at 96
+        // registers and two CTAs per SM; without them it runs three
         for (unsigned B = 0; B < nblocks; B += 2) {
-            const int4 r1a = __ldg(rec4 + 2 * (B + 1));
-            const int4 r1b = __ldg(rec4 + 2 * (B + 1) + 1);
-            const unsigned B2 = (B + 2 < nblocks) ? B + 2 : B + 1;
-            const int4 r2a = __ldg(rec4 + 2 * B2);
-            const int4 r2b = __ldg(rec4 + 2 * B2 + 1);
             block<R, 0>(L, cs);
-            trans<R>(L, r1a, r1b, sC, sS, n, nsw, stride, slot, cs.ce(0));
+            {
+                const int4 ra = __ldg(rec4 + 2 * (B + 1));
+                const int4 rb = __ldg(rec4 + 2 * (B + 1) + 1);
+                trans<R>(L, ra, rb, sC, sS, n, nsw, stride, slot, cs.ce(0));
+            }
             block<R, 1>(L, cs);
-            if (B + 2 < nblocks)
-                trans<R>(L, r2a, r2b, sC, sS, n, nsw, stride, slot, cs.ce(1));
+            if (B + 2 < nblocks) {
+                const int4 ra = __ldg(rec4 + 2 * (B + 2));
+                const int4 rb = __ldg(rec4 + 2 * (B + 2) + 1);
+                trans<R>(L, ra, rb, sC, sS, n, nsw, stride, slot, cs.ce(1));
+            }
         }
     }
     return (int)fminf(L.m[0], L.m[1]);

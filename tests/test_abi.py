@@ -53,6 +53,8 @@ def test_struct_sizes_match_header():
     assert ctypes.sizeof(_binding.QbfOptions) == 4 * 4 + 8 + 8 * 4  # 2 named + 6 reserved ints
     exp = 8 + 8 + 4 + 4 + 8 * 64 + 8 * 64 + 4 + 4 + 8 + 8 + 4 + 4 + 4 + 4 + 8 + 4 + 3 * 4
     assert ctypes.sizeof(_binding.QbfResult) == exp
+    # qbf_batch_info: double, uint64, 4 ints
+    assert ctypes.sizeof(_binding.QbfBatchInfo) == 8 + 8 + 4 * 4
 
 
 def test_default_options_and_version(lib):
