@@ -80,3 +80,15 @@ def test_batched_4096_equals_oracle_everywhere():
             v, a = oracle.blocked_min(Q)
             want = (float(v), a)
         assert (vmin[i], am[i]) == want, (i, Q.shape[0])
+
+
+def test_n44_chunked_top8_equals_oracle():
+    """n = 44 through the chunked, resumable API (16 chunks of 2^40 states, as
+    bench.py runs it): the merged top-8 equals the oracle's."""
+    g = _golden("gaussian_n44_f32.json")
+    Q = dev(inputs.gaussian_f32(44, seed=44))
+    c = qb.Chunked.start(Q, chunk_bits=4, top_k=8)
+    c.step(Q, max_chunks=16)
+    r = c.result()
+    assert (r.min_value, r.argmin) == (g["min"], g["argmin"])
+    assert [[v, i] for v, i in zip(r.topk_values, r.topk_indices)] == g["topk"]
