@@ -410,13 +410,22 @@ int qbf_danskin(const uint64_t *argmin_host, int n, int batch, const double *ups
  * loads the library holds until the process exits.  No cudaMalloc, cudaFree
  * or other allocating routine is called.
  *
- * Same arguments, semantics and result as qbf_solve, with these limits:
- * n <= QBF_NOALLOC_MAX_N, at most 2^16 prefixes (prefix_bits <= 16) and 2^20
- * suffix states per thread, at most 2^16 states in the certification window
- * (else QBF_EOVERFLOW).  Larger problems are rejected with QBF_EINVAL and a
- * message naming the limit.  The first call on a device looks up the scratch
- * array's device address (cudaGetSymbolAddress) with that device current; make
- * that first call before any stream capture.  All calls share the array and
+ * Same arguments as qbf_solve.  The answer (min_value, argmin, the top-k list)
+ * is qbf_solve's, whatever variant qbf_solve runs; this call always walks the
+ * int32 image, so scale_bits, error_bound and n_candidates are those of
+ * qbf_solve with variant = QBF_VARIANT_SPLIT.  opt->variant and opt->timing
+ * are ignored (walk_seconds stays 0).  Limits: n <= QBF_NOALLOC_MAX_N, at most
+ * 2^16 prefixes (prefix_bits <= 16) and 2^20 suffix states per thread, at
+ * most 2^16 states in the certification window (else QBF_EOVERFLOW, e.g. an
+ * exact top-k > 1 with massive ties, which qbf_solve's 2^22-state window
+ * still takes).  Larger problems are rejected with QBF_EINVAL and a message
+ * naming the limit.  The first call on a device looks up the scratch array's
+ * device address (cudaGetSymbolAddress) with that device current, and, under
+ * lazy module loading (the CUDA default), that lookup and the first kernel
+ * launches load the library's kernels and the array onto the device, which
+ * sets memory aside there; make that first call during set-up, before any
+ * stream capture (CUDA_MODULE_LOADING=EAGER moves the loading to process
+ * start).  Later calls set nothing aside.  All calls share the array and
  * each leaves its contents behind (every call resets what must start at zero);
  * calls whose GPU work overlaps race -- including with a concurrent qbf_solve --
  * so issue them from one thread at a time.  The call waits for `stream`.

@@ -4,6 +4,7 @@
     python tests/golden/make_golden.py n40      # n=40 FP32 headline instance: min, argmin, top-8
     python tests/golden/make_golden.py batched  # every n >= 26 instance of the 4096-instance batch
     python tests/golden/make_golden.py n44      # the n=44 FP32 instance of the chunked solver
+    python tests/golden/make_golden.py logz     # 4 of the 64 n=28 log Z instances in full
 
 Every value here comes from ``oracle`` (natural-order enumeration; exact int64
 for integer Q, canonical FP64 for float Q); nothing is taken from the GPU
@@ -103,5 +104,47 @@ def batched(n_min=26):
         json.dump(out, f, indent=0)
 
 
+LOGZ_INSTANCES = (0, 21, 42, 63)
+LOGZ_FD_ENTRIES = ((0, 0), (3, 17), (10, 27), (27, 27), (14, 2), (5, 6))
+LOGZ_FD_H = 1e-3
+
+
+def logz():
+    """log Z(beta) and E_beta[x x^T] of four instances of the n=28 log Z workload
+    (literal FP64 oracle, Kahan sums), and central differences of the oracle's
+    log Z for six entries of instance 0 (h = 1e-3)."""
+    Qs = inputs.config_logz()
+    betas = list(inputs.LOGZ_BETAS)
+    out = {"citation": "log Z(beta) = log sum_x exp(-beta x^T Q x) over all x (Eq. 1's objective) "
+                       "and E_beta[x_i x_j] by the CPU oracle's natural-order enumeration in FP64; "
+                       "central differences of the oracle's log Z.",
+           "generator": "paper_2310_19373_gb300.inputs.config_logz() (64 x n=28, seed 0)",
+           "betas": betas, "instances": []}
+    t0 = time.time()
+    for b in LOGZ_INSTANCES:
+        lz, E, vmin, am = oracle.logz(Qs[b], betas)
+        out["instances"].append({"index": b, "logz": [float(v) for v in lz],
+                                 "moment": [[[float(v) for v in row] for row in Eb] for Eb in E],
+                                 "min": float(vmin), "argmin": int(am)})
+        print(b, lz, round(time.time() - t0), flush=True)
+    fd = []
+    Q0 = Qs[0].astype(np.float64)
+    for (i, j) in LOGZ_FD_ENTRIES:
+        Qp, Qm = Q0.copy(), Q0.copy()
+        Qp[i, j] += LOGZ_FD_H
+        Qm[i, j] -= LOGZ_FD_H
+        lp, _, _, _ = oracle.logz(Qp, betas, moment=False)
+        lm, _, _, _ = oracle.logz(Qm, betas, moment=False)
+        fd.append({"i": i, "j": j,
+                   "dlogz": [float((a - c) / (2 * LOGZ_FD_H)) for a, c in zip(lp, lm)]})
+        print(i, j, fd[-1]["dlogz"], round(time.time() - t0), flush=True)
+    out["central_differences"] = {"instance": 0, "h": LOGZ_FD_H,
+                                  "note": "Q perturbed in FP64 (the FP32 instance widened)",
+                                  "entries": fd}
+    out["oracle_seconds"] = round(time.time() - t0, 1)
+    with open(os.path.join(HERE, "config_logz_n28.json"), "w") as f:
+        json.dump(out, f)
+
+
 if __name__ == "__main__":
-    {"n32": n32, "n40": n40, "n44": n44, "batched": batched}[sys.argv[1]]()
+    {"n32": n32, "n40": n40, "n44": n44, "batched": batched, "logz": logz}[sys.argv[1]]()

@@ -153,3 +153,38 @@ def test_logz_config_64x28():
         fd = (fp - fm) / (2 * hh)
         an = np.array([-beta * mom[0, j, i, k] for j, beta in enumerate(BETAS)])
         assert np.all(np.abs(fd - an) <= 1e-3 * np.maximum(np.abs(an), 1e-2)), (i, k, fd, an)
+
+
+def test_logz_config_64x28_four_instances_against_stored_oracle():
+    """Four of the 64 n = 28 instances (0, 21, 42, 63) in full against the
+    stored FP64 oracle: log Z and E[x x^T] at beta in {0.1, 1, 10} to 1e-6
+    relative, and the gradient -beta E[x_i x_j] against central differences
+    of the oracle's log Z (h = 1e-3) to 1e-4 relative."""
+    import json
+    import os
+
+    from conftest import GOLDEN
+
+    g = json.load(open(os.path.join(GOLDEN, "config_logz_n28.json")))
+    assert g["betas"] == BETAS
+    Qall = inputs.config_logz()
+    idx = [e["index"] for e in g["instances"]]
+    Qb = Qall[idx]
+    lz, vmin, am = run_forward(Qb, BETAS)
+    grad, mom = run_backward(Qb, BETAS)
+    for k, e in enumerate(g["instances"]):
+        assert (vmin[k], am[k]) == (e["min"], e["argmin"])
+        for j, beta in enumerate(BETAS):
+            assert abs(lz[k][j] - e["logz"][j]) <= RTOL * abs(e["logz"][j]) + 1e-9, (k, beta)
+            oE = np.array(e["moment"][j])
+            assert np.allclose(mom[k, j], oE, rtol=RTOL, atol=1e-9), (k, beta)
+        want = sum(-beta * np.array(e["moment"][j]) for j, beta in enumerate(BETAS))
+        assert np.allclose(grad[k], want, rtol=RTOL, atol=1e-9)
+    cd = g["central_differences"]
+    k0 = idx.index(cd["instance"])
+    for ent in cd["entries"]:
+        i, j2 = ent["i"], ent["j"]
+        for jb, beta in enumerate(BETAS):
+            an = -beta * mom[k0, jb, i, j2]
+            fd = ent["dlogz"][jb]
+            assert abs(fd - an) <= 1e-4 * max(abs(an), 1e-2), (i, j2, beta, fd, an)
