@@ -65,10 +65,11 @@ std::vector<Pool> g_pools;
 size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
 
 struct Layout {
-    size_t plan, ctr, res, kbuf, recs, pmin, flagged, cand, vals, qcopy, total;
+    size_t plan, ctr, res, kbuf, recs, pmin, flagged, cand, vals, qcopy, ftab, total;
 };
 
-Layout make_layout(size_t nrec, size_t npref, size_t qbytes, bool need_cand)
+Layout make_layout(size_t nrec, size_t npref, size_t qbytes, bool need_cand,
+                   size_t ftab_floats = 0)
 {
     Layout L;
     size_t o = 0;
@@ -92,6 +93,8 @@ Layout make_layout(size_t nrec, size_t npref, size_t qbytes, bool need_cand)
     o = align256(o + (need_cand ? sizeof(long long) * kCandCap : 0));
     L.qcopy = o;
     o = align256(o + qbytes);
+    L.ftab = o;
+    o = align256(o + sizeof(float) * ftab_floats);
     L.total = o;
     return L;
 }
@@ -344,7 +347,8 @@ int solve_one(const void *Q, bool host_q, int n, int dtype, const qbf_options *o
 
     const unsigned long long npref = g.p_hi - g.p_lo;
     const size_t qbytes = host_q ? dtype_size(dtype) * n * n : 0;
-    const Layout L = make_layout(1u << g.M, npref, qbytes, true);
+    const size_t ftab = defer ? walk_defer_table_floats(g.R, g.ns_tab) : 0;
+    const Layout L = make_layout(1u << g.M, npref, qbytes, true, ftab);
     Pool *P = nullptr;
     if ((rc = pool_get(L.total, sizeof(DevResult) + sizeof(Plan), &P)))
         return rc;
@@ -392,7 +396,8 @@ int solve_one(const void *Q, bool host_q, int n, int dtype, const qbf_options *o
         QBF_CUDA(launch_walk_naive(plan, a, num_sms(), s), "naive (min)");
     else if (defer)
         QBF_CUDA(launch_walk_defer(g.R, plan, recs, a, (const int *)(base + L.kbuf),
-                                   base + L.kbuf + sizeof(int) * kKbufInts, num_sms(), s),
+                                   base + L.kbuf + sizeof(int) * kKbufInts, num_sms(), s,
+                                   ftab ? (float *)(base + L.ftab) : nullptr),
                  "walk defer (min)");
     else if (mix)
         QBF_CUDA(launch_walk_mix(g.R, plan, recs, a, (const int *)(base + L.kbuf),
@@ -880,7 +885,8 @@ static int prefix_minima_impl(const void *Q_dev, int n, int dtype, int prefix_bi
     int rc = plan_geometry(n, o, &g);
     if (rc)
         return rc;
-    const Layout L = make_layout(1u << g.M, 0, 0, false);
+    const size_t ftab = defer ? walk_defer_table_floats(g.R, g.ns_tab) : 0;
+    const Layout L = make_layout(1u << g.M, 0, 0, false, ftab);
     Pool *P = nullptr;
     if ((rc = pool_get(L.total, sizeof(DevResult) + sizeof(Plan), &P)))
         return rc;
@@ -907,7 +913,8 @@ static int prefix_minima_impl(const void *Q_dev, int n, int dtype, int prefix_bi
     else if (defer)
         QBF_CUDA(launch_walk_defer(g.R, plan, (const Rec *)(base + L.recs), a,
                                    (const int *)(base + L.kbuf),
-                                   base + L.kbuf + sizeof(int) * kKbufInts, num_sms(), s),
+                                   base + L.kbuf + sizeof(int) * kKbufInts, num_sms(), s,
+                                   ftab ? (float *)(base + L.ftab) : nullptr),
                  "walk defer (min)");
     else if (mix)
         QBF_CUDA(launch_walk_mix(g.R, plan, (const Rec *)(base + L.recs), a,

@@ -99,9 +99,13 @@ cudaError_t ising_to_qubo(const void *J, const void *h, int n, int dtype, const 
 
 // qbf_walk_defer.cu: MIN walk with the in-block correction added after the
 // minimum over eight prefixes (same image bound and geometry as the two-pipe
-// walk); scratch_dev holds 130 floats
+// walk); scratch_dev holds 130 floats.  With ftab_dev (device memory of
+// walk_defer_table_floats(R, a.ns - 3) floats, when that is not 0) it runs the
+// table-driven form, else the record-driven one.
 cudaError_t launch_walk_defer(int R, const Plan *plan, const Rec *recs, const WalkArgs &a,
-                              const int *Kbuf_dev, void *scratch_dev, int num_sms, cudaStream_t s);
+                              const int *Kbuf_dev, void *scratch_dev, int num_sms, cudaStream_t s,
+                              float *ftab_dev = nullptr);
+size_t walk_defer_table_floats(int R, int nsw);
 
 // qbf_walk_mix.cu: MIN walk on both pipes (same image bound; eight prefixes per thread)
 cudaError_t launch_walk_mix(int R, const Plan *plan, const Rec *recs, const WalkArgs &a,

@@ -98,6 +98,335 @@ __global__ void __launch_bounds__(kWalkThreads, 3)
     }
 }
 
+// ---------------------------------------------------------------------------
+// The table-driven form of the deferred walk (used when the suffix table
+// fits, see launch_walk_defer).  The value of group b of a lane at suffix
+// state s splits exactly (Eq. 1 over the fixed-point image) as
+//     v_b(s) = F(s) + w_b(s),
+// F(s)   = sum_{i in s} lin_i + sum_{i<j in s} S_ij   (suffix only: the same
+//          for every lane and every group),
+// w_b(s) = H_b(p) + sum_{i in s} c_i(b, p),  c_i(b, p) = sum of S_ij over the
+//          set group and prefix variables j        (the lane part).
+// Flipping suffix variable i moves w_b by +-c_i(b, p), a constant of the walk,
+// so the low-bit fields never change and a block transition only adds the
+// mid bit's +-c_i(b, p) to the eight values.  min_b v_b(s) = min_b w_b(s) +
+// F(s): the lane-invariant F(gray(t)) of every suffix step t is a table built
+// once per solve (2^nsw floats, exact: |F| < 2^23), which each warp stages
+// block by block into shared memory with cp.async.  Per step and lane: 4 packed
+// adds, three three-input mins and one min for the eight values, and per pair
+// of steps one packed add of (F(t-1), F(t)) and one three-input min into the
+// running minimum.  |w| and |F| stay below 2^23, so every operation is exact.
+// ---------------------------------------------------------------------------
+
+constexpr int kDefer2MaxM = 14;  // largest 2^M blocks of 2^R states per lane (table <= 4 MB)
+
+// F(gray(t)) for t < 2^nsw on the image of the plan (int64 sums, then FP32)
+__global__ void defer2_ftab_kernel(const Plan *__restrict__ plan, int nsw, float *ftab)
+{
+    const int n = plan->n;
+    const unsigned N = 1u << nsw;
+    for (unsigned t = blockIdx.x * blockDim.x + threadIdx.x; t < N; t += gridDim.x * blockDim.x) {
+        const unsigned x = t ^ (t >> 1);
+        long long f = 0;
+        for (unsigned r = x; r; r &= r - 1) {
+            const int i = __ffs(r) - 1;
+            f += plan->lin[i];
+            for (unsigned q = r & (r - 1); q; q &= q - 1)
+                f += plan->S[i * n + (__ffs(q) - 1)];
+        }
+        ftab[t] = (float)f;
+    }
+}
+
+namespace dfr2 {
+
+using f32x2::u64;
+
+template <int R>
+struct Lane {
+    u64 w[4];      // lane parts of the eight values, pairs (b0 = 0, b0 = 1) of (b2 b1)
+    u64 GF[4][R];  // lane parts c_l(b, p) of the low-bit fields (constant)
+    float m[2];    // running minima (two chains)
+};
+
+// cp.async of 16 bytes, global -> shared
+__device__ __forceinline__ void cp16(void *dst_smem, const void *src)
+{
+    const unsigned d = (unsigned)__cvta_generic_to_shared(dst_smem);
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(d), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_wait() { asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory"); }
+
+// One block of 2^R states, parity pi (a runtime value: it only reverses the
+// flip of variable R - 1 at u = 2^(R-1), so one unrolled copy serves both).
+// State u = 0 is the block's first state; Fs holds its 2^R table values.
+template <int R>
+__device__ __forceinline__ void block(Lane<R> &L, const float *Fs, int pi)
+{
+    float tp = 0.f;
+    float4 f4 = make_float4(0.f, 0.f, 0.f, 0.f);
+#pragma unroll
+    for (int u = 0; u < (1 << R); ++u) {
+        if (u > 0) {
+            const int l = ctz_c(u);
+            const int nb = ((u ^ (u >> 1)) >> l) & 1;
+            if (l == R - 1) {
+                if (nb ^ pi) {
+#pragma unroll
+                    for (int s = 0; s < 4; ++s)
+                        L.w[s] = f32x2::add(L.w[s], L.GF[s][l]);
+                } else {
+#pragma unroll
+                    for (int s = 0; s < 4; ++s)
+                        L.w[s] = f32x2::sub(L.w[s], L.GF[s][l]);
+                }
+            } else {
+#pragma unroll
+                for (int s = 0; s < 4; ++s)
+                    L.w[s] = nb ? f32x2::add(L.w[s], L.GF[s][l]) : f32x2::sub(L.w[s], L.GF[s][l]);
+            }
+        }
+        float x[8];
+#pragma unroll
+        for (int s = 0; s < 4; ++s)
+            f32x2::unpack(L.w[s], x[2 * s], x[2 * s + 1]);
+        const float t = dfr::min8(x);
+        if ((u & 3) == 0)
+            f4 = *reinterpret_cast<const float4 *>(Fs + u);
+        if (u & 1) {
+            // states u - 1 and u: one packed add of their F, one three-input min
+            const float fa = (u & 2) ? f4.z : f4.x;
+            const float fb = (u & 2) ? f4.w : f4.y;
+            const u64 y = f32x2::add(f32x2::pack(tp, t), f32x2::pack(fa, fb));
+            float lo, hi;
+            f32x2::unpack(y, lo, hi);
+            L.m[(u >> 1) & 1] = f32x2::min3(L.m[(u >> 1) & 1], lo, hi);
+        } else {
+            tp = t;
+        }
+    }
+}
+
+// Transition into block B >= 1: mid variable R + j, j = CTZ(B), takes bit j of
+// gray(B); the eight values move by +-c_{R+j}(b, p): the lane part (sCf) plus
+// the lane-invariant group terms (sE: per mid variable and direction, the
+// eight signed values as two float4).
+template <int R>
+__device__ __forceinline__ void mid_flip(Lane<R> &L, unsigned B, const float *sCf, int stride,
+                                         int slot, const float4 *sE)
+{
+    const int j = __ffs(B) - 1;
+    const int up = ((B ^ (B >> 1)) >> j) & 1;
+    const float c = sCf[j * stride + slot];
+    const float sc = up ? c : -c;
+    const u64 y = f32x2::pack(sc, sc);
+    const float4 e01 = sE[(j * 2 + up) * 2];
+    const float4 e23 = sE[(j * 2 + up) * 2 + 1];
+    L.w[0] = f32x2::add(L.w[0], f32x2::add(y, f32x2::pack(e01.x, e01.y)));
+    L.w[1] = f32x2::add(L.w[1], f32x2::add(y, f32x2::pack(e01.z, e01.w)));
+    L.w[2] = f32x2::add(L.w[2], f32x2::add(y, f32x2::pack(e23.x, e23.y)));
+    L.w[3] = f32x2::add(L.w[3], f32x2::add(y, f32x2::pack(e23.z, e23.w)));
+}
+
+// Lane set-up for prefix p (variables nsg..n-1): the eight start values (F of
+// the empty suffix is 0, so they are the values themselves), the lane parts
+// of the low-bit fields, and those of the mid-bit fields (sCf).
+template <int R>
+__device__ __forceinline__ void setup(Lane<R> &L, unsigned long long p, int n, int nsg,
+                                      const int *sS, const int *sLin, float *sCf, int stride,
+                                      int slot)
+{
+    const int nsw = nsg - 3;
+    const int kp = n - nsg;
+    int va = 0;
+    for (int j = 0; j < kp; ++j) {
+        if (!((p >> j) & 1))
+            continue;
+        const int vj = nsg + j;
+        int row = sLin[vj];
+        for (int jj = j + 1; jj < kp; ++jj)
+            if ((p >> jj) & 1)
+                row += sS[vj * n + nsg + jj];
+        va += row;
+    }
+    int gf[3];
+#pragma unroll
+    for (int t = 0; t < 3; ++t) {
+        int f = sLin[nsw + t];
+        for (int j = 0; j < kp; ++j)
+            if ((p >> j) & 1)
+                f += sS[(nsw + t) * n + nsg + j];
+        gf[t] = f;
+    }
+    const int s01 = sS[nsw * n + nsw + 1], s02 = sS[nsw * n + nsw + 2];
+    const int s12 = sS[(nsw + 1) * n + nsw + 2];
+    const int v000 = va, v001 = va + gf[0];
+    const int v010 = va + gf[1], v011 = v010 + gf[0] + s01;
+    const int v100 = va + gf[2], v101 = v100 + gf[0] + s02;
+    const int v110 = v010 + gf[2] + s12, v111 = v011 + gf[2] + s02 + s12;
+    L.w[0] = f32x2::pack((float)v000, (float)v001);
+    L.w[1] = f32x2::pack((float)v010, (float)v011);
+    L.w[2] = f32x2::pack((float)v100, (float)v101);
+    L.w[3] = f32x2::pack((float)v110, (float)v111);
+#pragma unroll
+    for (int ii = 0; ii < R; ++ii) {
+        int c = 0;
+        for (int j = 0; j < kp; ++j)
+            if ((p >> j) & 1)
+                c += sS[ii * n + nsg + j];
+        const int s0 = sS[ii * n + nsw], s1 = sS[ii * n + nsw + 1], s2 = sS[ii * n + nsw + 2];
+        L.GF[0][ii] = f32x2::pack((float)c, (float)(c + s0));
+        L.GF[1][ii] = f32x2::pack((float)(c + s1), (float)(c + s1 + s0));
+        L.GF[2][ii] = f32x2::pack((float)(c + s2), (float)(c + s2 + s0));
+        L.GF[3][ii] = f32x2::pack((float)(c + s1 + s2), (float)(c + s0 + s1 + s2));
+    }
+    for (int ii = R; ii < nsw; ++ii) {
+        int c = 0;
+        for (int j = 0; j < kp; ++j)
+            if ((p >> j) & 1)
+                c += sS[ii * n + nsg + j];
+        sCf[(ii - R) * stride + slot] = (float)c;
+    }
+    L.m[0] = L.m[1] = __int_as_float(0x7f800000);  // +inf: every state is compared
+}
+
+// The whole walk of one lane: blocks in Gray order of the mid bits, each
+// block's F staged by the warp into its double buffer one block ahead.
+template <int R>
+__device__ __forceinline__ int walk_min(Lane<R> &L, int nsw, const float *ftab, float *fbuf,
+                                        int lane, const float *sCf, int stride, int slot,
+                                        const float4 *sE)
+{
+    constexpr int BS = 1 << R;  // F values per block; a multiple of 4 (R >= 2)
+    const unsigned nblocks = 1u << (nsw - R);
+    if (lane < BS / 4)
+        cp16(fbuf + 4 * lane, ftab + 4 * lane);
+    cp_commit();
+    for (unsigned B = 0; B < nblocks; ++B) {
+        const float *cur = fbuf + (B & 1) * 64;
+        if (B + 1 < nblocks) {
+            if (lane < BS / 4)
+                cp16(fbuf + ((B + 1) & 1) * 64 + 4 * lane, ftab + (size_t)(B + 1) * BS + 4 * lane);
+            cp_commit();
+            cp_wait<1>();
+        } else {
+            cp_wait<0>();
+        }
+        __syncwarp();
+        if (B > 0)
+            mid_flip<R>(L, B, sCf, stride, slot, sE);
+        block<R>(L, cur, (int)(B & 1));
+        __syncwarp();  // every lane is done with cur before it is refilled
+    }
+    return (int)fminf(L.m[0], L.m[1]);
+}
+
+}  // namespace dfr2
+
+// The table-driven MIN walk: same geometry, groups and output as
+// walk_defer_min_kernel (a.ns = nsw + 3), R = kRMax.  Three CTAs of 256
+// threads per SM (at most 80 registers).
+__global__ void __launch_bounds__(kWalkThreads, 3)
+    walk_defer2_min_kernel(const Plan *__restrict__ plan, const float *__restrict__ ftab, WalkArgs a)
+{
+    constexpr int R = kRMax;
+    extern __shared__ __align__(16) int smem[];
+    const int n = a.n;
+    const int nsg = a.ns;
+    const int nsw = nsg - 3;
+    const int nmid = nsw - R;
+    float *fbufs = reinterpret_cast<float *>(smem);  // per warp: two blocks of 64 F values
+    float4 *sE = reinterpret_cast<float4 *>(fbufs + (kWalkThreads / 32) * 128);
+    float *sCf = reinterpret_cast<float *>(sE + nmid * 4);
+    int *sS = reinterpret_cast<int *>(sCf + nmid * kWalkThreads);
+    int *sLin = sS + n * n;
+    for (int e = threadIdx.x; e < n * n; e += blockDim.x)
+        sS[e] = plan->S[e];
+    for (int e = threadIdx.x; e < n; e += blockDim.x)
+        sLin[e] = plan->lin[e];
+    __syncthreads();
+    // group terms of every mid variable i, both directions: sign * (b0 S_i,nsw +
+    // b1 S_i,nsw+1 + b2 S_i,nsw+2) for the eight groups b
+    for (int e = threadIdx.x; e < nmid * 2; e += blockDim.x) {
+        const int i = R + (e >> 1);
+        const float sg = (e & 1) ? 1.f : -1.f;
+        const float s0 = (float)sS[i * n + nsw], s1 = (float)sS[i * n + nsw + 1];
+        const float s2 = (float)sS[i * n + nsw + 2];
+        sE[e * 2] = make_float4(0.f, sg * s0, sg * s1, sg * (s1 + s0));
+        sE[e * 2 + 1] = make_float4(sg * s2, sg * (s2 + s0), sg * (s1 + s2), sg * (s0 + s1 + s2));
+    }
+    __syncthreads();
+    if (plan->status != QBF_OK)
+        return;
+    const int lane = threadIdx.x & 31;
+    float *fbuf = fbufs + (threadIdx.x >> 5) * 128;
+    const int stride = blockDim.x, slot = threadIdx.x;
+    while (true) {
+        unsigned long long item = 0;
+        if (lane == 0)
+            item = atomicAdd(&a.ctr->items[kModeMin], 1ull);
+        item = __shfl_sync(0xffffffffu, item, 0);
+        if (item >= a.nitems)
+            break;
+        const unsigned long long i = a.p_lo + item * 32 + lane;
+        const bool active = i < a.p_hi;
+        const unsigned long long p = active ? i : a.p_lo;
+        dfr2::Lane<R> L;
+        dfr2::setup<R>(L, p, n, nsg, sS, sLin, sCf, stride, slot);
+        const int mi = dfr2::walk_min<R>(L, nsw, ftab, fbuf, lane, sCf, stride, slot, sE);
+        if (active)
+            a.pmin[p - a.p_lo] = mi;
+        int wm = active ? mi : INT_MAX;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1)
+            wm = min(wm, __shfl_xor_sync(0xffffffffu, wm, o));
+        if (lane == 0)
+            atomicMin(&a.ctr->gmin, wm);
+    }
+}
+
+size_t walk_defer_table_floats(int R, int nsw)
+{
+    if (R != kRMax || nsw < R || nsw - R > kDefer2MaxM)
+        return 0;
+    return (size_t)1 << nsw;
+}
+
+static cudaError_t launch_defer2(const Plan *plan, float *ftab, const WalkArgs &a, int num_sms,
+                                 cudaStream_t s)
+{
+    const int nsw = a.ns - 3;
+    const unsigned N = 1u << nsw;
+    defer2_ftab_kernel<<<(N + 255) / 256 < 4096 ? (N + 255) / 256 : 4096, 256, 0, s>>>(plan, nsw,
+                                                                                      ftab);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess)
+        return e;
+    const int nmid = nsw - kRMax;
+    const size_t smem = sizeof(float) * (kWalkThreads / 32) * 128 + sizeof(float4) * nmid * 4 +
+                        sizeof(float) * nmid * kWalkThreads + sizeof(int) * (a.n * a.n + a.n);
+    auto k = walk_defer2_min_kernel;
+    e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess)
+        return e;
+    int bps = 0;
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, k, kWalkThreads, smem);
+    if (e != cudaSuccess)
+        return e;
+    if (bps < 1)
+        bps = 1;
+    const unsigned long long need = (a.nitems + (kWalkThreads / 32) - 1) / (kWalkThreads / 32);
+    unsigned long long grid = (unsigned long long)num_sms * bps;
+    if (grid > need)
+        grid = need;
+    if (grid < 1)
+        grid = 1;
+    k<<<(unsigned)grid, kWalkThreads, smem, s>>>(plan, ftab, a);
+    return cudaGetLastError();
+}
+
 namespace {
 
 // C[pi][u] = K[pi][1] + ... + K[pi][u] (exact in int32: |C| < 2^23) and the
@@ -150,10 +479,13 @@ static cudaError_t launch_defer_r(const Plan *plan, const Rec *recs, const WalkA
 }
 
 cudaError_t launch_walk_defer(int R, const Plan *plan, const Rec *recs, const WalkArgs &a,
-                              const int *Kbuf_dev, void *scratch_dev, int num_sms, cudaStream_t s)
+                              const int *Kbuf_dev, void *scratch_dev, int num_sms, cudaStream_t s,
+                              float *ftab_dev)
 {
     if (R < 1 || R > kRMax)
         return cudaErrorInvalidValue;
+    if (ftab_dev && walk_defer_table_floats(R, a.ns - 3) > 0)
+        return launch_defer2(plan, ftab_dev, a, num_sms, s);
     float *tab = static_cast<float *>(scratch_dev);  // 130 floats
     k_defer_tables_kernel<<<1, 32, 0, s>>>(Kbuf_dev, R, tab);
     cudaError_t e = cudaGetLastError();
