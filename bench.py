@@ -307,7 +307,7 @@ def run_reference(args, rank):
 VARIANTS = {"auto": 0, "field": 1, "split": 2, "tc": 3, "f32": 4, "mix": 5, "naive": 6, "defer": 7}
 
 
-def run_profile_case(n, variant=0):
+def run_profile_case(n, variant=0, prefix_bits=-1):
     import torch
 
     import __graft_entry__
@@ -318,10 +318,10 @@ def run_profile_case(n, variant=0):
 
     Q = torch.from_numpy(inputs.gaussian_f32(n, seed=0)).cuda()
     for _ in range(2):
-        sol = qb.solve(Q, timing=True, variant=variant)
+        sol = qb.solve(Q, timing=True, variant=variant, prefix_bits=prefix_bits)
     torch.cuda.synchronize()
-    print(json.dumps({"profile_n": n, "min_value": sol.min_value, "argmin": sol.argmin,
-                      "walk_ms": sol.walk_seconds * 1e3}))
+    print(json.dumps({"profile_n": n, "prefix_bits": sol.prefix_bits, "min_value": sol.min_value,
+                      "argmin": sol.argmin, "walk_ms": sol.walk_seconds * 1e3}))
 
 
 def run_profile_batched(count, variant=0):
@@ -576,6 +576,8 @@ def main():
     ap.add_argument("--profile-n", type=int, default=0,
                     help="profiling target: two solves of an n-variable Gaussian FP32 instance, "
                          "no timing (for ncu)")
+    ap.add_argument("--prefix-bits", type=int, default=-1,
+                    help="with --profile-n: prefix bits of the solve (-1: the planner's choice)")
     ap.add_argument("--variant", default="auto", choices=list(VARIANTS),
                     help="kernel form of the headline solve (auto: the library's choice)")
     ap.add_argument("--profile-batched", type=int, default=0,
@@ -595,7 +597,7 @@ def main():
         run_reference(args, rank)
         return
     if args.profile_n:
-        run_profile_case(args.profile_n, VARIANTS[args.variant])
+        run_profile_case(args.profile_n, VARIANTS[args.variant], args.prefix_bits)
         return
     if args.alu_microbench:
         run_alu_microbench()
