@@ -313,13 +313,16 @@ int qbf_solve_batched_info(const void *const *Q_dev, const int *n, const int *dt
  * qbf_tune -- autotuner of the batched solver, per n and element class.
  *
  * For every n in [n_min, n_max] (1 <= n_min <= n_max <= QBF_BATCH_MAX_N) it
- * builds a synthetic batch of that n on the current device (upper-triangular
+ * builds synthetic batches of that n on the current device (upper-triangular
  * instances, uniform in [-1, 1] for float dtypes, integers in [-50, 50] for
- * integer dtypes; about 2^37 states, at most 4096 instances), times
- * qbf_solve_batched over the suffix width walked per lane (which fixes the
- * prefix width k = n - suffix bits, Section 3.1's split) and the number of
- * resident 128-thread CTAs per SM of the walk kernel, and keeps the fastest
- * pair (suffix width first, then CTAs per SM at that width).  The choices
+ * integer dtypes; c and 2c instances, c = 2^36 / 2^n, at most 2048) and
+ * scores each configuration by the difference of their qbf_solve_batched
+ * times: the steady-state cost of c instances, as in a large mixed batch,
+ * without the last partial wave of one small launch.  It searches the suffix
+ * width walked per lane (the five widest the instance allows; it fixes the
+ * prefix width k = n - suffix bits, Section 3.1's split) and then the number
+ * of resident 128-thread CTAs per SM of the walk kernel, and keeps the best
+ * pair.  The choices
  * take effect at once in this process for the current device, and one line
  * per n is appended to `cache_path`:
  *     qbf-tune-v1 <device name> <SM count> <class> <n> <suffix bits> <CTAs/SM> <seconds>

@@ -950,17 +950,21 @@ __global__ void tune_fill_kernel(void *buf, int n, int dtype, unsigned long long
 
 }  // namespace
 
-// One n of qbf_tune: time the batch for every suffix width at the largest CTA
-// count, then every CTA count at the best width; returns QBF_OK and the choice.
+// One n of qbf_tune.  A configuration is scored by the time difference between
+// a synthetic batch of 2c instances and one of c instances (c = 2^36 / 2^n,
+// at most 2048): the difference is the steady-state cost of c instances, free
+// of the last partial wave of work items, which in a single small launch
+// favours short walks but vanishes in a large mixed batch.  The suffix widths
+// searched are the five widest the instance allows (narrower ones only add
+// per-prefix set-up), at the largest CTA count; then every CTA count at the
+// best width.
 static int tune_one_n(int n, int dtype, cudaStream_t s, int *best_ns, int *best_ctas,
                       double *best_sec)
 {
     const int esz = dtsize(dtype);
-    // about 2^37 states (at most 4096 instances): the work queue then runs many
-    // waves, as in a large mixed batch, so the choice reflects the steady
-    // state and not the tail of one small launch
-    const unsigned long long count =
-        std::max<unsigned long long>(1, std::min<unsigned long long>(4096, (1ull << 37) >> n));
+    const unsigned long long c =
+        std::max<unsigned long long>(1, std::min<unsigned long long>(2048, (1ull << 36) >> n));
+    const unsigned long long count = 2 * c;
     const unsigned long long per = (unsigned long long)n * n;
     void *buf = nullptr;
     B_CUDA(cudaMalloc(&buf, per * count * esz), "cudaMalloc(tuning batch)");
@@ -979,50 +983,61 @@ static int tune_one_n(int n, int dtype, cudaStream_t s, int *best_ns, int *best_
     cudaEvent_t e0 = nullptr, e1 = nullptr;
     cudaEventCreate(&e0);
     cudaEventCreate(&e1);
-    int rc = QBF_OK;
-    auto time_one = [&](int ns, int ctas, double *sec) -> int {
+    // best of two timed solves of the first `m` instances (after one that
+    // builds the graph of this layout)
+    auto time_m = [&](int ns, int ctas, unsigned long long m, double *sec) -> int {
         qbf_options o;
         qbf_default_options(&o);
         o.batch_suffix_bits = ns;
-        // first call builds the graph for this layout; then the median of three
-        int r = solve_batched(ptr.data(), nn.data(), dt.data(), (int)count, &o, vmin.data(),
+        int r = solve_batched(ptr.data(), nn.data(), dt.data(), (int)m, &o, vmin.data(),
                               am.data(), s, nullptr, nullptr, ctas);
         if (r)
             return r;
-        float t[3];
-        for (int k = 0; k < 3; ++k) {
+        float best = 1e30f;
+        for (int k = 0; k < 2; ++k) {
             cudaEventRecord(e0, s);
-            r = solve_batched(ptr.data(), nn.data(), dt.data(), (int)count, &o, vmin.data(),
+            r = solve_batched(ptr.data(), nn.data(), dt.data(), (int)m, &o, vmin.data(),
                               am.data(), s, nullptr, nullptr, ctas);
             cudaEventRecord(e1, s);
             cudaEventSynchronize(e1);
             if (r)
                 return r;
-            cudaEventElapsedTime(&t[k], e0, e1);
+            float t = 0.f;
+            cudaEventElapsedTime(&t, e0, e1);
+            best = std::min(best, t);
         }
-        std::sort(t, t + 3);
-        *sec = t[1] * 1e-3;
+        *sec = best * 1e-3;
         return QBF_OK;
     };
+    auto score = [&](int ns, int ctas, double *sec) -> int {
+        double t1 = 0, t2 = 0;
+        int r = time_m(ns, ctas, c, &t1);
+        if (r == QBF_OK)
+            r = time_m(ns, ctas, count, &t2);
+        *sec = t2 - t1;
+        return r;
+    };
+    int rc = QBF_OK;
     const int bps = walk_bps(kModeMin);
     const int nw = std::max(n, kBatchMinN);
     const int ns_hi = std::max(kBatchR, std::min(kBatchMaxNS, nw - 5));
+    const int ns_lo = std::max(kBatchR, ns_hi - 4);
     double bsec = 1e300;
     int bns = ns_hi, bct = bps;
-    for (int ns = kBatchR; ns <= ns_hi && rc == QBF_OK; ++ns) {
+    for (int ns = ns_lo; ns <= ns_hi && rc == QBF_OK; ++ns) {
         double t = 0;
-        rc = time_one(ns, bps, &t);
+        rc = score(ns, bps, &t);
         if (rc == QBF_OK && t < bsec) {
             bsec = t;
             bns = ns;
         }
     }
-    for (int c = 1; c < bps && rc == QBF_OK; ++c) {
+    for (int cc = 1; cc < bps && rc == QBF_OK; ++cc) {
         double t = 0;
-        rc = time_one(bns, c, &t);
+        rc = score(bns, cc, &t);
         if (rc == QBF_OK && t < bsec) {
             bsec = t;
-            bct = c;
+            bct = cc;
         }
     }
     cudaEventDestroy(e0);
