@@ -57,6 +57,9 @@ constexpr int kWarpSmemInts =
     (512 + QBF_BATCH_MAX_N * QBF_BATCH_MAX_N + QBF_BATCH_MAX_N + 128 +
      2 * (kBatchMaxNS - kBatchR) * 32 + 3) & ~3;
 constexpr unsigned long long kBatchCandCap = 1ull << 20;
+// resident CTAs per SM asked of the table-driven deferred MIN kernel (bounded
+// by the 41.6 KB of shared memory per CTA: five fit in 228 KB)
+constexpr int kBatchDeferCtas = 5;
 
 // per-instance certification details, filled on the device (qbf_batch_info)
 struct BatchInfoDev {
@@ -80,6 +83,7 @@ struct BatchArgs {
     unsigned long long *cand_idx;
     unsigned *cand_inst;
     unsigned long long cap;
+    const float *ftab;  // suffix tables of the table-driven deferred walk
     int mix;  // MIN walk for instances whose image fits 2^23: 0 none (int32),
               // 1 the two-pipe walk, 2 the deferred-correction walk
 };
@@ -108,8 +112,13 @@ __device__ __forceinline__ int find_instance(const BatchDesc *d, int count, unsi
     return lo;
 }
 
-template <int MODE>
-__global__ void __launch_bounds__(kBatchThreads) batched_walk_kernel(BatchArgs a)
+// MIXK: the MIN walk of instances whose image fits 2^23 (a.mix): 0 none
+// (int32 throughout; also the EMIT pass), 1 the two-pipe walk, 2 the
+// table-driven deferred walk.  One instantiation per form keeps the register
+// count of each to what its own paths need.
+template <int MODE, int MIXK>
+__global__ void __launch_bounds__(kBatchThreads, (MODE == kModeMin && MIXK == 2) ? kBatchDeferCtas : 1)
+    batched_walk_kernel(BatchArgs a)
 {
     __shared__ __align__(16) int sm[kBatchWarps][kWarpSmemInts];
     const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -119,6 +128,7 @@ __global__ void __launch_bounds__(kBatchThreads) batched_walk_kernel(BatchArgs a
     int cur = -1, n = 0, ns = 0, tau = 0, ok = 0, exact = 0, use_mix = 0;
     unsigned long long nprefix = 0, item_off = 0;
     const int4 *rec4 = nullptr;
+    const float *ftab_i = nullptr;
     const unsigned long long total =
         (MODE == kModeMin) ? a.total_items : (unsigned long long)a.ctr->flagged;
 
@@ -140,6 +150,7 @@ __global__ void __launch_bounds__(kBatchThreads) batched_walk_kernel(BatchArgs a
             nprefix = d.nprefix;
             item_off = d.item_off;
             rec4 = reinterpret_cast<const int4 *>(a.recs + d.rec_off);
+            ftab_i = (MIXK == 2 && d.ftab_off != ~0ull) ? a.ftab + d.ftab_off : nullptr;
             ok = (plan->status == QBF_OK);
             sLin = sS + n * n;
             sK = sLin + n;
@@ -152,35 +163,30 @@ __global__ void __launch_bounds__(kBatchThreads) batched_walk_kernel(BatchArgs a
                 const int k = a.K[inst * 128 + e];
                 const int kf = __float_as_int((float)k);  // exact when the image fits 2^23
                 sK[e] = k;
-                if (a.mix == 1)
+                if (MIXK == 1)
                     sKx[e] = make_int4(kf, kf, k, 0);
             }
-            if (a.mix == 2) {
-                // C[pi][u] = K[pi][1] + ... + K[pi][u] (K[pi][0] = 0): a warp
-                // scan over u = lane and u = 32 + lane for each parity
-                float *sCd = reinterpret_cast<float *>(sKx);
-#pragma unroll
-                for (int pi = 0; pi < 2; ++pi) {
-                    int c0 = a.K[inst * 128 + pi * 64 + lane];
-                    int c1 = a.K[inst * 128 + pi * 64 + 32 + lane];
-#pragma unroll
-                    for (int o = 1; o < 32; o <<= 1) {
-                        const int t0 = __shfl_up_sync(0xffffffffu, c0, o);
-                        const int t1 = __shfl_up_sync(0xffffffffu, c1, o);
-                        if (lane >= o) {
-                            c0 += t0;
-                            c1 += t1;
-                        }
-                    }
-                    c1 += __shfl_sync(0xffffffffu, c0, 31);
-                    sCd[pi * 64 + lane] = (float)c0;  // exact: |C| < 2^23
-                    sCd[pi * 64 + 32 + lane] = (float)c1;
+            if (MODE == kModeMin && MIXK == 2 && ftab_i) {
+                // the table-driven deferred walk: the first 128 words of the
+                // slice are the warp's double buffer of F values, then the
+                // group terms of every mid variable, both directions
+                __syncwarp();
+                const int nsw = ns - 3;
+                float4 *sE = reinterpret_cast<float4 *>(sm[w] + 128);
+                for (int e = lane; e < (nsw - kBatchR) * 2; e += 32) {
+                    const int i = kBatchR + (e >> 1);
+                    const float sg = (e & 1) ? 1.f : -1.f;
+                    const float s0 = (float)sS[i * n + nsw], s1 = (float)sS[i * n + nsw + 1];
+                    const float s2 = (float)sS[i * n + nsw + 2];
+                    sE[e * 2] = make_float4(0.f, sg * s0, sg * s1, sg * (s1 + s0));
+                    sE[e * 2 + 1] =
+                        make_float4(sg * s2, sg * (s2 + s0), sg * (s1 + s2), sg * (s0 + s1 + s2));
                 }
             }
             // eight-prefix walks: every partial sum must be exact in FP32, and
             // the lane needs R walked bits below its three group bits
-            use_mix = (MODE == kModeMin) && a.mix && ok && ns >= kBatchR + 3 &&
-                      plan->vhat <= (long long)kF32Vmax;
+            use_mix = (MODE == kModeMin) && MIXK && ok && ns >= kBatchR + 3 &&
+                      plan->vhat <= (long long)kF32Vmax && (MIXK != 2 || ftab_i);
             if (MODE == kModeEmit && ok) {
                 const long long t = (long long)a.gmin[inst] + plan->window;
                 tau = (int)(t > (long long)INT_MAX ? (long long)INT_MAX : t);
@@ -196,12 +202,15 @@ __global__ void __launch_bounds__(kBatchThreads) batched_walk_kernel(BatchArgs a
         const unsigned long long p = active ? pl : 0;
         if constexpr (MODE == kModeMin) {
             int m;
-            if (use_mix && a.mix == 2) {
-                dfr::Lane<kBatchR> L;
-                dfr::setup<kBatchR>(L, p, n, ns, sS, sLin, sC, 32, lane);
-                m = dfr::walk_min_rt<kBatchR>(L, n, ns, rec4, sC, sS, 32, lane,
-                                              reinterpret_cast<const float *>(sKx));
-            } else if (use_mix) {
+            if (MIXK == 2 && use_mix) {
+                dfr2::Lane<kBatchR> L;
+                float *sCf = reinterpret_cast<float *>(sC);
+                dfr2::setup<kBatchR>(L, p, n, ns, sS, sLin, sCf, 32, lane, nullptr);
+                m = dfr2::walk_min<kBatchR>(L, ns - 3, ftab_i, reinterpret_cast<float *>(sm[w]),
+                                            lane, sCf, 32, lane,
+                                            reinterpret_cast<const float4 *>(sm[w] + 128),
+                                            nullptr);
+            } else if (MIXK == 1 && use_mix) {
                 mix::Lane<kBatchR> L;
                 mix::setup<kBatchR>(L, p, n, ns, sS, sLin, sC, 32, lane);
                 m = mix::walk_min_rt<kBatchR>(L, n, ns, rec4, sC, sS, 32, lane, sKx);
@@ -378,6 +387,31 @@ __global__ void batched_rescore_kernel(const BatchDesc *desc, const unsigned lon
     }
 }
 
+// Suffix tables of the table-driven deferred walk: F(gray(t)) for t <
+// 2^(ns - 3) on the instance's image (int64 sums, exact in FP32 since the
+// image fits 2^23 whenever the walk uses them).  One CTA per instance.
+__global__ void batched_ftab_kernel(const BatchDesc *desc, const Plan *plans, float *ftab)
+{
+    const BatchDesc d = desc[blockIdx.x];
+    if (d.ftab_off == ~0ull)
+        return;
+    const Plan *plan = plans + blockIdx.x;
+    const int n = d.n;
+    const unsigned N = 1u << (d.ns - 3);
+    float *out = ftab + d.ftab_off;
+    for (unsigned t = threadIdx.x; t < N; t += blockDim.x) {
+        const unsigned x = t ^ (t >> 1);
+        long long f = 0;
+        for (unsigned r = x; r; r &= r - 1) {
+            const int i = __ffs(r) - 1;
+            f += plan->lin[i];
+            for (unsigned q = r & (r - 1); q; q &= q - 1)
+                f += plan->S[i * n + (__ffs(q) - 1)];
+        }
+        out[t] = (float)f;
+    }
+}
+
 // sigma, window and MIN walk form of every instance (the walk choice repeats
 // the MIN kernel's eligibility test)
 __global__ void batched_info_kernel(const BatchDesc *desc, int count, const Plan *plans, int mix,
@@ -416,12 +450,13 @@ __global__ void batched_argmin_kernel(const unsigned long long *cand_idx,
 
 struct BLayout {
     size_t desc, plans, K, recs, item_min, flagged, gmin, best_key, best_idx, status, lowest,
-        ctr, cand_idx, cand_inst, keys, info, total;
+        ctr, cand_idx, cand_inst, keys, info, ftab, total;
 };
 
 size_t a256(size_t x) { return (x + 255) & ~(size_t)255; }
 
-BLayout blayout(int count, unsigned long long nrec, unsigned long long items)
+BLayout blayout(int count, unsigned long long nrec, unsigned long long items,
+                unsigned long long nftab)
 {
     BLayout L;
     size_t o = 0;
@@ -446,6 +481,7 @@ BLayout blayout(int count, unsigned long long nrec, unsigned long long items)
     L.cand_inst = take(sizeof(unsigned) * kBatchCandCap);
     L.keys = take(sizeof(unsigned long long) * kBatchCandCap);
     L.info = take(sizeof(BatchInfoDev) * count);
+    L.ftab = take(sizeof(float) * nftab);
     L.total = o;
     return L;
 }
@@ -503,15 +539,22 @@ struct BatchState {
 std::mutex g_bmu;
 std::vector<BatchState> g_bstate;
 
-int walk_bps(int mode)
+// resident CTAs per SM of the MIN kernel of walk form `mix`, or of the EMIT kernel
+int walk_bps(int mode, int mix = 0)
 {
     int b = 0;
     cudaError_t e;
-    if (mode == kModeMin)
-        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, batched_walk_kernel<kModeMin>,
+    if (mode != kModeMin)
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, batched_walk_kernel<kModeEmit, 0>,
+                                                          kBatchThreads, 0);
+    else if (mix == 2)
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, batched_walk_kernel<kModeMin, 2>,
+                                                          kBatchThreads, 0);
+    else if (mix == 1)
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, batched_walk_kernel<kModeMin, 1>,
                                                           kBatchThreads, 0);
     else
-        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, batched_walk_kernel<kModeEmit>,
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, batched_walk_kernel<kModeMin, 0>,
                                                           kBatchThreads, 0);
     return (e != cudaSuccess || b < 1) ? 1 : b;
 }
@@ -604,6 +647,8 @@ int enqueue_batch(BatchState &B, const BLayout &L, const BStage &S, int count,
     batched_prepare_kernel<<<count, 256, 0, s>>>(desc, plans, (int *)(d + L.status),
                                                  mix ? kF32Vmax : (long long)INT_MAX);
     batched_tables_kernel<<<count, 256, 0, s>>>(desc, plans, recs, K);
+    if (mix == 2)
+        batched_ftab_kernel<<<count, 256, 0, s>>>(desc, plans, (float *)(d + L.ftab));
     BatchArgs a;
     memset(&a, 0, sizeof(a));
     a.desc = desc;
@@ -620,13 +665,19 @@ int enqueue_batch(BatchState &B, const BLayout &L, const BStage &S, int count,
     a.cand_inst = (unsigned *)(d + L.cand_inst);
     a.cap = kBatchCandCap;
     a.mix = mix;
-    batched_walk_kernel<kModeMin><<<grid_min, kBatchThreads, 0, s>>>(a);
+    a.ftab = (const float *)(d + L.ftab);
+    if (mix == 2)
+        batched_walk_kernel<kModeMin, 2><<<grid_min, kBatchThreads, 0, s>>>(a);
+    else if (mix == 1)
+        batched_walk_kernel<kModeMin, 1><<<grid_min, kBatchThreads, 0, s>>>(a);
+    else
+        batched_walk_kernel<kModeMin, 0><<<grid_min, kBatchThreads, 0, s>>>(a);
     const int fb = (int)std::min<unsigned long long>((items + 255) / 256, 8192);
     batched_flag_kernel<<<fb, 256, 0, s>>>(desc, count, plans, a.item_min, gmin, items,
                                            (unsigned *)(d + L.flagged), lowest, ctr);
     batched_lowest_kernel<<<(count + 255) / 256, 256, 0, s>>>(count, lowest,
                                                               (unsigned *)(d + L.flagged), ctr);
-    batched_walk_kernel<kModeEmit><<<grid_emit, kBatchThreads, 0, s>>>(a);
+    batched_walk_kernel<kModeEmit, 0><<<grid_emit, kBatchThreads, 0, s>>>(a);
     unsigned long long *keys = (unsigned long long *)(d + L.keys);
     batched_rescore_kernel<<<512, 256, 0, s>>>(desc, a.cand_idx, a.cand_inst, ctr, kBatchCandCap,
                                                keys, best_key, info);
@@ -695,7 +746,7 @@ int solve_batched_mode(const void *const *Q, const int *n, const int *dtype, int
 
     // plan every instance
     std::vector<BatchDesc> desc(count);
-    unsigned long long items = 0, nrec = 0;
+    unsigned long long items = 0, nrec = 0, nftab = 0;
     int ns_max = 0;
     for (int i = 0; i < count; ++i) {
         if (!Q[i])
@@ -719,11 +770,18 @@ int solve_batched_mode(const void *const *Q, const int *n, const int *dtype, int
         d.nprefix = 1ull << (d.n - d.ns);
         d.item_off = items;
         d.rec_off = nrec;
+        d.ftab_off = ~0ull;
         items += (d.nprefix + 31) / 32;
         nrec += 1ull << (d.ns - kBatchR);
+        if (mix == 2 && d.ns >= kBatchR + 3) {
+            // suffix table of the table-driven deferred walk: 2^(ns - 3) floats,
+            // a multiple of 64, so every block of it starts 256-byte aligned
+            d.ftab_off = nftab;
+            nftab += 1ull << (d.ns - 3);
+        }
         ns_max = std::max(ns_max, d.ns);
     }
-    const BLayout L = blayout(count, nrec, items);
+    const BLayout L = blayout(count, nrec, items, nftab);
     const BStage S = bstage(count);
     bool relayout = false;
     if (B.dev_bytes < L.total) {
@@ -762,7 +820,7 @@ int solve_batched_mode(const void *const *Q, const int *n, const int *dtype, int
                 }
         ctas = B.tab_ctas[bc][bn];
     }
-    const int bps = walk_bps(kModeMin);
+    const int bps = walk_bps(kModeMin, mix);
     const int cps = (ctas > 0 && ctas < bps) ? ctas : bps;
     const int grid_min = (int)std::max<unsigned long long>(
         1, std::min<unsigned long long>((unsigned long long)nsm * cps,
@@ -806,7 +864,7 @@ int solve_batched_mode(const void *const *Q, const int *n, const int *dtype, int
     B_CUDA(cudaGraphLaunch(B.exec, s), "graph launch");
     B_CUDA(cudaStreamSynchronize(s), "batched solve");
     if (kernel_launches)
-        *kernel_launches = 11;
+        *kernel_launches = (mix == 2) ? 12 : 11;
 
     const unsigned long long *bk = (const unsigned long long *)(h + S.best_key);
     const unsigned long long *bi = (const unsigned long long *)(h + S.best_idx);
@@ -1018,7 +1076,7 @@ static int tune_one_n(int n, int dtype, cudaStream_t s, int *best_ns, int *best_
         return r;
     };
     int rc = QBF_OK;
-    const int bps = walk_bps(kModeMin);
+    const int bps = walk_bps(kModeMin, 2);  // the AUTO form the tuned solves run
     const int nw = std::max(n, kBatchMinN);
     const int ns_hi = std::max(kBatchR, std::min(kBatchMaxNS, nw - 5));
     const int ns_lo = std::max(kBatchR, ns_hi - 4);

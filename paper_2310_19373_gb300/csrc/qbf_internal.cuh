@@ -76,6 +76,8 @@ struct BatchDesc {
     unsigned long long nprefix;    // 2^(n - ns)
     unsigned long long item_off;   // first global work item (32 prefixes each)
     unsigned long long rec_off;    // first walk record
+    unsigned long long ftab_off;   // first suffix-table entry (table-driven deferred
+                                   // walk), or ~0 when the instance has none
 };
 
 }  // namespace qbf

@@ -119,6 +119,9 @@ __global__ void __launch_bounds__(kWalkThreads, 3)
 // ---------------------------------------------------------------------------
 
 constexpr int kDefer2MaxM = 14;  // largest 2^M blocks of 2^R states per lane (table <= 4 MB)
+constexpr int kDefer2Threads = 256;
+constexpr int kDefer2CtasPerSm = 3;  // at most 80 registers
+
 
 // F(gray(t)) for t < 2^nsw on the image of the plan (int64 sums, then FP32)
 __global__ void defer2_ftab_kernel(const Plan *__restrict__ plan, int nsw, float *ftab)
@@ -138,197 +141,10 @@ __global__ void defer2_ftab_kernel(const Plan *__restrict__ plan, int nsw, float
     }
 }
 
-namespace dfr2 {
-
-using f32x2::u64;
-
-template <int R>
-struct Lane {
-    u64 w[4];      // lane parts of the eight values, pairs (b0 = 0, b0 = 1) of (b2 b1)
-    u64 GF[4][R];  // lane parts c_l(b, p) of the low-bit fields (constant)
-    float m[2];    // running minima (two chains)
-};
-
-// cp.async of 16 bytes, global -> shared
-__device__ __forceinline__ void cp16(void *dst_smem, const void *src)
-{
-    const unsigned d = (unsigned)__cvta_generic_to_shared(dst_smem);
-    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(d), "l"(src) : "memory");
-}
-__device__ __forceinline__ void cp_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
-template <int N>
-__device__ __forceinline__ void cp_wait() { asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory"); }
-
-// One block of 2^R states, parity pi (a runtime value: it only reverses the
-// flip of variable R - 1 at u = 2^(R-1), so one unrolled copy serves both).
-// State u = 0 is the block's first state; Fs holds its 2^R table values.
-template <int R>
-__device__ __forceinline__ void block(Lane<R> &L, const float *Fs, int pi)
-{
-    float tp = 0.f;
-    float4 f4 = make_float4(0.f, 0.f, 0.f, 0.f);
-#pragma unroll
-    for (int u = 0; u < (1 << R); ++u) {
-        if (u > 0) {
-            const int l = ctz_c(u);
-            const int nb = ((u ^ (u >> 1)) >> l) & 1;
-            if (l == R - 1) {
-                if (nb ^ pi) {
-#pragma unroll
-                    for (int s = 0; s < 4; ++s)
-                        L.w[s] = f32x2::add(L.w[s], L.GF[s][l]);
-                } else {
-#pragma unroll
-                    for (int s = 0; s < 4; ++s)
-                        L.w[s] = f32x2::sub(L.w[s], L.GF[s][l]);
-                }
-            } else {
-#pragma unroll
-                for (int s = 0; s < 4; ++s)
-                    L.w[s] = nb ? f32x2::add(L.w[s], L.GF[s][l]) : f32x2::sub(L.w[s], L.GF[s][l]);
-            }
-        }
-        float x[8];
-#pragma unroll
-        for (int s = 0; s < 4; ++s)
-            f32x2::unpack(L.w[s], x[2 * s], x[2 * s + 1]);
-        const float t = dfr::min8(x);
-        if ((u & 3) == 0)
-            f4 = *reinterpret_cast<const float4 *>(Fs + u);
-        if (u & 1) {
-            // states u - 1 and u: one packed add of their F, one three-input min
-            const float fa = (u & 2) ? f4.z : f4.x;
-            const float fb = (u & 2) ? f4.w : f4.y;
-            const u64 y = f32x2::add(f32x2::pack(tp, t), f32x2::pack(fa, fb));
-            float lo, hi;
-            f32x2::unpack(y, lo, hi);
-            L.m[(u >> 1) & 1] = f32x2::min3(L.m[(u >> 1) & 1], lo, hi);
-        } else {
-            tp = t;
-        }
-    }
-}
-
-// Transition into block B >= 1: mid variable R + j, j = CTZ(B), takes bit j of
-// gray(B); the eight values move by +-c_{R+j}(b, p): the lane part (sCf) plus
-// the lane-invariant group terms (sE: per mid variable and direction, the
-// eight signed values as two float4).
-template <int R>
-__device__ __forceinline__ void mid_flip(Lane<R> &L, unsigned B, const float *sCf, int stride,
-                                         int slot, const float4 *sE)
-{
-    const int j = __ffs(B) - 1;
-    const int up = ((B ^ (B >> 1)) >> j) & 1;
-    const float c = sCf[j * stride + slot];
-    const float sc = up ? c : -c;
-    const u64 y = f32x2::pack(sc, sc);
-    const float4 e01 = sE[(j * 2 + up) * 2];
-    const float4 e23 = sE[(j * 2 + up) * 2 + 1];
-    L.w[0] = f32x2::add(L.w[0], f32x2::add(y, f32x2::pack(e01.x, e01.y)));
-    L.w[1] = f32x2::add(L.w[1], f32x2::add(y, f32x2::pack(e01.z, e01.w)));
-    L.w[2] = f32x2::add(L.w[2], f32x2::add(y, f32x2::pack(e23.x, e23.y)));
-    L.w[3] = f32x2::add(L.w[3], f32x2::add(y, f32x2::pack(e23.z, e23.w)));
-}
-
-// Lane set-up for prefix p (variables nsg..n-1): the eight start values (F of
-// the empty suffix is 0, so they are the values themselves), the lane parts
-// of the low-bit fields, and those of the mid-bit fields (sCf).
-template <int R>
-__device__ __forceinline__ void setup(Lane<R> &L, unsigned long long p, int n, int nsg,
-                                      const int *sS, const int *sLin, float *sCf, int stride,
-                                      int slot)
-{
-    const int nsw = nsg - 3;
-    const int kp = n - nsg;
-    int va = 0;
-    for (int j = 0; j < kp; ++j) {
-        if (!((p >> j) & 1))
-            continue;
-        const int vj = nsg + j;
-        int row = sLin[vj];
-        for (int jj = j + 1; jj < kp; ++jj)
-            if ((p >> jj) & 1)
-                row += sS[vj * n + nsg + jj];
-        va += row;
-    }
-    int gf[3];
-#pragma unroll
-    for (int t = 0; t < 3; ++t) {
-        int f = sLin[nsw + t];
-        for (int j = 0; j < kp; ++j)
-            if ((p >> j) & 1)
-                f += sS[(nsw + t) * n + nsg + j];
-        gf[t] = f;
-    }
-    const int s01 = sS[nsw * n + nsw + 1], s02 = sS[nsw * n + nsw + 2];
-    const int s12 = sS[(nsw + 1) * n + nsw + 2];
-    const int v000 = va, v001 = va + gf[0];
-    const int v010 = va + gf[1], v011 = v010 + gf[0] + s01;
-    const int v100 = va + gf[2], v101 = v100 + gf[0] + s02;
-    const int v110 = v010 + gf[2] + s12, v111 = v011 + gf[2] + s02 + s12;
-    L.w[0] = f32x2::pack((float)v000, (float)v001);
-    L.w[1] = f32x2::pack((float)v010, (float)v011);
-    L.w[2] = f32x2::pack((float)v100, (float)v101);
-    L.w[3] = f32x2::pack((float)v110, (float)v111);
-#pragma unroll
-    for (int ii = 0; ii < R; ++ii) {
-        int c = 0;
-        for (int j = 0; j < kp; ++j)
-            if ((p >> j) & 1)
-                c += sS[ii * n + nsg + j];
-        const int s0 = sS[ii * n + nsw], s1 = sS[ii * n + nsw + 1], s2 = sS[ii * n + nsw + 2];
-        L.GF[0][ii] = f32x2::pack((float)c, (float)(c + s0));
-        L.GF[1][ii] = f32x2::pack((float)(c + s1), (float)(c + s1 + s0));
-        L.GF[2][ii] = f32x2::pack((float)(c + s2), (float)(c + s2 + s0));
-        L.GF[3][ii] = f32x2::pack((float)(c + s1 + s2), (float)(c + s0 + s1 + s2));
-    }
-    for (int ii = R; ii < nsw; ++ii) {
-        int c = 0;
-        for (int j = 0; j < kp; ++j)
-            if ((p >> j) & 1)
-                c += sS[ii * n + nsg + j];
-        sCf[(ii - R) * stride + slot] = (float)c;
-    }
-    L.m[0] = L.m[1] = __int_as_float(0x7f800000);  // +inf: every state is compared
-}
-
-// The whole walk of one lane: blocks in Gray order of the mid bits, each
-// block's F staged by the warp into its double buffer one block ahead.
-template <int R>
-__device__ __forceinline__ int walk_min(Lane<R> &L, int nsw, const float *ftab, float *fbuf,
-                                        int lane, const float *sCf, int stride, int slot,
-                                        const float4 *sE)
-{
-    constexpr int BS = 1 << R;  // F values per block; a multiple of 4 (R >= 2)
-    const unsigned nblocks = 1u << (nsw - R);
-    if (lane < BS / 4)
-        cp16(fbuf + 4 * lane, ftab + 4 * lane);
-    cp_commit();
-    for (unsigned B = 0; B < nblocks; ++B) {
-        const float *cur = fbuf + (B & 1) * 64;
-        if (B + 1 < nblocks) {
-            if (lane < BS / 4)
-                cp16(fbuf + ((B + 1) & 1) * 64 + 4 * lane, ftab + (size_t)(B + 1) * BS + 4 * lane);
-            cp_commit();
-            cp_wait<1>();
-        } else {
-            cp_wait<0>();
-        }
-        __syncwarp();
-        if (B > 0)
-            mid_flip<R>(L, B, sCf, stride, slot, sE);
-        block<R>(L, cur, (int)(B & 1));
-        __syncwarp();  // every lane is done with cur before it is refilled
-    }
-    return (int)fminf(L.m[0], L.m[1]);
-}
-
-}  // namespace dfr2
 
 // The table-driven MIN walk: same geometry, groups and output as
-// walk_defer_min_kernel (a.ns = nsw + 3), R = kRMax.  Three CTAs of 256
-// threads per SM (at most 80 registers).
-__global__ void __launch_bounds__(kWalkThreads, 3)
+// walk_defer_min_kernel (a.ns = nsw + 3), R = kRMax.
+__global__ void __launch_bounds__(kDefer2Threads, kDefer2CtasPerSm)
     walk_defer2_min_kernel(const Plan *__restrict__ plan, const float *__restrict__ ftab, WalkArgs a)
 {
     constexpr int R = kRMax;
@@ -338,9 +154,10 @@ __global__ void __launch_bounds__(kWalkThreads, 3)
     const int nsw = nsg - 3;
     const int nmid = nsw - R;
     float *fbufs = reinterpret_cast<float *>(smem);  // per warp: two blocks of 64 F values
-    float4 *sE = reinterpret_cast<float4 *>(fbufs + (kWalkThreads / 32) * 128);
+    ulonglong2 *sGFx = reinterpret_cast<ulonglong2 *>(fbufs + (kDefer2Threads / 32) * 128);
+    float4 *sE = reinterpret_cast<float4 *>(sGFx + (R - kDefer2RegBits) * 2 * kDefer2Threads);
     float *sCf = reinterpret_cast<float *>(sE + nmid * 4);
-    int *sS = reinterpret_cast<int *>(sCf + nmid * kWalkThreads);
+    int *sS = reinterpret_cast<int *>(sCf + nmid * kDefer2Threads);
     int *sLin = sS + n * n;
     for (int e = threadIdx.x; e < n * n; e += blockDim.x)
         sS[e] = plan->S[e];
@@ -374,8 +191,8 @@ __global__ void __launch_bounds__(kWalkThreads, 3)
         const bool active = i < a.p_hi;
         const unsigned long long p = active ? i : a.p_lo;
         dfr2::Lane<R> L;
-        dfr2::setup<R>(L, p, n, nsg, sS, sLin, sCf, stride, slot);
-        const int mi = dfr2::walk_min<R>(L, nsw, ftab, fbuf, lane, sCf, stride, slot, sE);
+        dfr2::setup<R>(L, p, n, nsg, sS, sLin, sCf, stride, slot, sGFx);
+        const int mi = dfr2::walk_min<R>(L, nsw, ftab, fbuf, lane, sCf, stride, slot, sE, sGFx);
         if (active)
             a.pmin[p - a.p_lo] = mi;
         int wm = active ? mi : INT_MAX;
@@ -405,25 +222,27 @@ static cudaError_t launch_defer2(const Plan *plan, float *ftab, const WalkArgs &
     if (e != cudaSuccess)
         return e;
     const int nmid = nsw - kRMax;
-    const size_t smem = sizeof(float) * (kWalkThreads / 32) * 128 + sizeof(float4) * nmid * 4 +
-                        sizeof(float) * nmid * kWalkThreads + sizeof(int) * (a.n * a.n + a.n);
+    const size_t smem = sizeof(float) * (kDefer2Threads / 32) * 128 +
+                        sizeof(ulonglong2) * (kRMax - kDefer2RegBits) * 2 * kDefer2Threads +
+                        sizeof(float4) * nmid * 4 +
+                        sizeof(float) * nmid * kDefer2Threads + sizeof(int) * (a.n * a.n + a.n);
     auto k = walk_defer2_min_kernel;
     e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess)
         return e;
     int bps = 0;
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, k, kWalkThreads, smem);
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, k, kDefer2Threads, smem);
     if (e != cudaSuccess)
         return e;
     if (bps < 1)
         bps = 1;
-    const unsigned long long need = (a.nitems + (kWalkThreads / 32) - 1) / (kWalkThreads / 32);
+    const unsigned long long need = (a.nitems + (kDefer2Threads / 32) - 1) / (kDefer2Threads / 32);
     unsigned long long grid = (unsigned long long)num_sms * bps;
     if (grid > need)
         grid = need;
     if (grid < 1)
         grid = 1;
-    k<<<(unsigned)grid, kWalkThreads, smem, s>>>(plan, ftab, a);
+    k<<<(unsigned)grid, kDefer2Threads, smem, s>>>(plan, ftab, a);
     return cudaGetLastError();
 }
 
