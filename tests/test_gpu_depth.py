@@ -88,3 +88,18 @@ def test_prefix_minima_fixed_matches_whole_space_run(variant):
         assert s1 == s2
         w = 1 << (k - fix)
         assert np.array_equal(part.cpu().numpy(), full.cpu().numpy()[fv * w:(fv + 1) * w])
+
+
+@pytest.mark.parametrize("variant", [qb.QBF_VARIANT_SPLIT_DEFER, qb.QBF_VARIANT_AUTO])
+def test_deep_suffix_takes_the_record_driven_walk(variant):
+    """A lane walking more than 2^14 blocks (here 2^15: 21 walked bits) does not
+    fit the table-driven form's suffix table and runs the record-driven
+    deferred walk; its per-prefix minima and the solve still equal the oracle."""
+    n, k = 26, 2  # suffix 24 = 3 group bits + 21 walked bits
+    Q = inputs.gaussian_f32(n, seed=26)
+    Qd = torch.from_numpy(Q).cuda()
+    pm, sigma = qb.prefix_minima(Qd, k, qb.QBF_VARIANT_SPLIT_DEFER)
+    want, _ = oracle.segment_minima(fixed_point_image(Q, sigma), 1 << (n - k), 1 << k)
+    assert np.array_equal(pm.cpu().numpy().astype(np.int64), want)
+    s = qb.solve(Qd, variant=variant, prefix_bits=k)
+    assert (s.min_value, s.argmin) == oracle.blocked_min(Q)
