@@ -508,7 +508,10 @@ int qbf_tc_selftest(const uint16_t *A_host, const uint16_t *B_host, float *D_hos
  *
  * op: 0 IADD3, 1 IMNMX, 2 3-input integer min, 3 FADD, 4 FFMA, 5 FMNMX,
  *     6 3-input FMNMX, 7 packed FADD (f32x2), 8 IADD3+IMNMX pair,
- *     9 FADD+FMNMX pair.
+ *     9 FADD+FMNMX pair, 10 ex2.approx (exponential unit), 11 FP64 add,
+ *     12 integer multiply-add, 13 int32 -> FP32 -> int32 conversion pair
+ *     (each conversion counts one).  Operations are counted as written in PTX:
+ *     the assembler may merge consecutive dependent two-input mins.
  * Writes scalar lane operations per SM clock per SM to *ops_per_clk_sm (a
  * packed f32x2 add counts two, each instruction of a pair counts one), the
  * SM clock seen during the run to *sm_mhz and the elapsed device time to

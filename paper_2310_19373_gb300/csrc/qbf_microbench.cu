@@ -6,6 +6,12 @@
 // instruction class, fills every SM with one wave of resident blocks, and is
 // timed with CUDA events.  The result is lane operations per SM clock per SM
 // (a packed f32x2 add counts as two; each instruction of a pair counts one).
+// The figures count the operations written in PTX: the assembler may merge two
+// consecutive dependent mins of a chain into one three-input min, so the
+// two-input min classes can read up to twice the instruction rate (in the
+// walk kernels every ALU instruction, two- or three-input, holds the pipe two
+// cycles, per ncu).  Ops 10-13 (the exponential unit, FP64 add, integer
+// multiply-add, int/float conversions) serve the log Z and rescoring rooflines.
 #include <cstdint>
 #include <vector>
 
@@ -25,6 +31,7 @@ __global__ void __launch_bounds__(kMbThreads) alu_kernel(int iters, unsigned see
     int x[8], y[8];
     float f[8], g[8];
     unsigned long long p[8];
+    double dd[8];
     const int ia = (int)(seed ^ threadIdx.x), ib = (int)(seed >> 3);
     const float fa = 1.0f + (float)(threadIdx.x & 7) * 1e-7f, fb = 0.999f;
     const unsigned long long pc = ((unsigned long long)__float_as_uint(fa) << 32) | __float_as_uint(fb);
@@ -34,7 +41,9 @@ __global__ void __launch_bounds__(kMbThreads) alu_kernel(int iters, unsigned see
         f[j] = (float)(x[j] & 0xffff) * 1e-3f;
         g[j] = f[j] + 1.0f;
         p[j] = ((unsigned long long)__float_as_uint(f[j]) << 32) | __float_as_uint(g[j]);
+        dd[j] = (double)f[j];
     }
+    const double da = 1.0000001;
     __syncthreads();
     const long long t0 = clock64();
     for (int it = 0; it < iters; ++it) {
@@ -59,6 +68,16 @@ __global__ void __launch_bounds__(kMbThreads) alu_kernel(int iters, unsigned see
                     asm volatile("min.f32 %0, %0, %1, %2;" : "+f"(g[j]) : "f"(fa), "f"(fb));
                 if constexpr (OP == 7)
                     asm volatile("add.rn.f32x2 %0, %0, %1;" : "+l"(p[j]) : "l"(pc));
+                if constexpr (OP == 10)  // f <- 2^(-f): stays near 0.64, never folds
+                    asm volatile("{.reg .f32 t; neg.f32 t, %0; ex2.approx.ftz.f32 %0, t;}"
+                                 : "+f"(f[j]));
+                if constexpr (OP == 11)
+                    asm volatile("add.rn.f64 %0, %0, %1;" : "+d"(dd[j]) : "d"(da));
+                if constexpr (OP == 12)
+                    asm volatile("mad.lo.s32 %0, %0, %1, %2;" : "+r"(x[j]) : "r"(ia), "r"(ib));
+                if constexpr (OP == 13)  // int -> float -> int chain: one I2F and one F2I
+                    asm volatile("{.reg .f32 t; cvt.rn.f32.s32 t, %0; cvt.rzi.s32.f32 %0, t;}"
+                                 : "+r"(x[j]));
             }
         }
     }
@@ -66,7 +85,7 @@ __global__ void __launch_bounds__(kMbThreads) alu_kernel(int iters, unsigned see
     unsigned acc = 0;
     for (int j = 0; j < 8; ++j)
         acc ^= (unsigned)x[j] ^ (unsigned)y[j] ^ __float_as_uint(f[j]) ^ __float_as_uint(g[j]) ^
-               (unsigned)p[j] ^ (unsigned)(p[j] >> 32);
+               (unsigned)p[j] ^ (unsigned)(p[j] >> 32) ^ (unsigned)__double2loint(dd[j]);
     if (acc == 0x12345678u)
         sink[0] = acc;
     if (threadIdx.x == 0)
@@ -120,7 +139,8 @@ cudaError_t run_op(int iters, double *ops_per_clk_sm, double *sm_mhz, double *se
     for (long long c : h)
         mean_cyc += (double)c;
     mean_cyc /= grid;
-    const double ops_per_thread = (double)iters * kRounds * 8 * ((OP == 7 || OP >= 8) ? 2 : 1);
+    const double ops_per_thread =
+        (double)iters * kRounds * 8 * ((OP == 7 || OP == 8 || OP == 9 || OP == 13) ? 2 : 1);
     const double ops_per_sm = ops_per_thread * kMbThreads * bps;
     *ops_per_clk_sm = ops_per_sm / mean_cyc;
     *seconds = ms * 1e-3;
@@ -145,6 +165,10 @@ cudaError_t run_alu_microbench(int op, double *ops_per_clk_sm, double *sm_mhz, d
     case 7: return run_op<7>(iters, ops_per_clk_sm, sm_mhz, seconds, s);
     case 8: return run_op<8>(iters, ops_per_clk_sm, sm_mhz, seconds, s);
     case 9: return run_op<9>(iters, ops_per_clk_sm, sm_mhz, seconds, s);
+    case 10: return run_op<10>(iters / 4, ops_per_clk_sm, sm_mhz, seconds, s);
+    case 11: return run_op<11>(iters / 16, ops_per_clk_sm, sm_mhz, seconds, s);
+    case 12: return run_op<12>(iters, ops_per_clk_sm, sm_mhz, seconds, s);
+    case 13: return run_op<13>(iters / 4, ops_per_clk_sm, sm_mhz, seconds, s);
     default: return cudaErrorInvalidValue;
     }
 }
