@@ -316,6 +316,116 @@ int check_common(const void *Q, int n, int dtype, qbf_result *out)
     return QBF_OK;
 }
 
+// ---- graph replay of repeated solves ----------------------------------------
+
+// One solve attempt is fixed by its matrix pointer, shape, options and the
+// scratch pool it runs in; the kernels read Q at replay time, so new contents
+// in the same buffer are solved afresh.
+struct SolveKey {
+    const void *Q;
+    int n, dtype, top_k, variant, prefix_bits, fix_bits;
+    uint64_t fix_value;
+    void *dev, *host;
+    size_t total;
+    bool operator==(const SolveKey &o) const { return memcmp(this, &o, sizeof(*this)) == 0; }
+};
+
+struct SolveGraph {
+    SolveKey key;
+    cudaGraphExec_t exec = nullptr;
+    unsigned long long used = 0;
+    bool seen = false;
+};
+
+constexpr int kSolveGraphs = 8;  // attempts remembered per device (least recently used out)
+
+struct DevGraphs {
+    cudaStream_t cap = nullptr;
+    SolveGraph slot[kSolveGraphs];
+    unsigned long long tick = 0;
+};
+std::vector<DevGraphs> g_graphs;
+
+bool graphs_enabled()
+{
+    const char *e = getenv("QBF_NO_SOLVE_GRAPHS");
+    return !(e && *e && *e != '0');
+}
+
+// Run one attempt: directly the first time its key is seen, captured into a
+// graph and replayed from the second time on.  Called with g_mu held.
+template <class F>
+int run_cached(const SolveKey &key, F &&enqueue, cudaStream_t s)
+{
+    int dev = 0;
+    QBF_CUDA(cudaGetDevice(&dev), "cudaGetDevice");
+    if ((int)g_graphs.size() <= dev)
+        g_graphs.resize(dev + 1);
+    DevGraphs &G = g_graphs[dev];
+    ++G.tick;
+    SolveGraph *hit = nullptr, *victim = &G.slot[0];
+    for (SolveGraph &sg : G.slot) {
+        if (sg.seen && sg.key == key) {
+            hit = &sg;
+            break;
+        }
+        if (!sg.seen || sg.used < victim->used)
+            victim = &sg;
+    }
+    if (!hit) {
+        if (victim->exec)
+            cudaGraphExecDestroy(victim->exec);
+        victim->exec = nullptr;
+        victim->key = key;
+        victim->seen = true;
+        victim->used = G.tick;
+        return enqueue(s);
+    }
+    hit->used = G.tick;
+    if (!hit->exec) {
+        if (!G.cap)
+            QBF_CUDA(cudaStreamCreateWithFlags(&G.cap, cudaStreamNonBlocking), "capture stream");
+        cudaGraph_t graph = nullptr;
+        QBF_CUDA(cudaStreamBeginCapture(G.cap, cudaStreamCaptureModeThreadLocal), "begin capture");
+        const int rc = enqueue(G.cap);
+        const cudaError_t ce = cudaStreamEndCapture(G.cap, &graph);
+        if (rc || ce != cudaSuccess) {
+            if (graph)
+                cudaGraphDestroy(graph);
+            hit->seen = false;
+            return rc ? rc : cuda_err(ce, "end capture");
+        }
+        const cudaError_t ie = cudaGraphInstantiate(&hit->exec, graph, 0);
+        cudaGraphDestroy(graph);
+        if (ie != cudaSuccess) {
+            hit->exec = nullptr;
+            hit->seen = false;
+            return cuda_err(ie, "graph instantiate");
+        }
+    }
+    QBF_CUDA(cudaGraphLaunch(hit->exec, s), "graph launch");
+    return QBF_OK;
+}
+
+void release_graphs()
+{
+    int cur = 0;
+    cudaGetDevice(&cur);
+    for (size_t d = 0; d < g_graphs.size(); ++d) {
+        DevGraphs &G = g_graphs[d];
+        cudaSetDevice((int)d);
+        for (SolveGraph &sg : G.slot) {
+            if (sg.exec)
+                cudaGraphExecDestroy(sg.exec);
+            sg = SolveGraph();
+        }
+        if (G.cap)
+            cudaStreamDestroy(G.cap);
+        G.cap = nullptr;
+    }
+    cudaSetDevice(cur);
+}
+
 int solve_one(const void *Q, bool host_q, int n, int dtype, const qbf_options *opt_in,
               qbf_result *out, cudaStream_t s)
 {
@@ -350,19 +460,10 @@ int solve_one(const void *Q, bool host_q, int n, int dtype, const qbf_options *o
     const size_t ftab = defer ? walk_defer_table_floats(g.R, g.ns_tab) : 0;
     const Layout L = make_layout(1u << g.M, npref, qbytes, true, ftab);
     Pool *P = nullptr;
-    if ((rc = pool_get(L.total, sizeof(DevResult) + sizeof(Plan), &P)))
+    if ((rc = pool_get(L.total, sizeof(DevResult) + sizeof(Plan) + 16, &P)))
         return rc;
     char *base = (char *)P->dev;
-    const void *Qdev = Q;
-    if (host_q) {
-        QBF_CUDA(cudaMemcpyAsync(base + L.qcopy, Q, qbytes, cudaMemcpyHostToDevice, s),
-                 "copy Q to device");
-        Qdev = base + L.qcopy;
-    }
-    if ((rc = enqueue_prepare(Qdev, n, dtype, g, base, L, s,
-                              tc ? kTcVmax : (f32 ? kF32Vmax : (long long)INT_MAX))))
-        return rc;
-
+    const void *Qdev = host_q ? (const void *)(base + L.qcopy) : Q;
     Plan *plan = (Plan *)(base + L.plan);
     Counters *ctr = (Counters *)(base + L.ctr);
     const Rec *recs = (const Rec *)(base + L.recs);
@@ -371,6 +472,20 @@ int solve_one(const void *Q, bool host_q, int n, int dtype, const qbf_options *o
     unsigned long long *cand = (unsigned long long *)(base + L.cand);
     long long *vals = (long long *)(base + L.vals);
     DevResult *dres = (DevResult *)(base + L.res);
+    char *h = (char *)P->host;
+    const bool is_int = (dtype == QBF_I32 || dtype == QBF_I16);
+    cudaEvent_t ev[2] = {nullptr, nullptr};
+    // Every stream operation of one attempt, on stream st: replayable as a
+    // graph (no host decision inside; the host reads the results afterwards)
+    auto enqueue = [&](cudaStream_t s) -> int {
+    if (host_q) {
+        QBF_CUDA(cudaMemcpyAsync(base + L.qcopy, Q, qbytes, cudaMemcpyHostToDevice, s),
+                 "copy Q to device");
+    }
+    int erc = enqueue_prepare(Qdev, n, dtype, g, base, L, s,
+                              tc ? kTcVmax : (f32 ? kF32Vmax : (long long)INT_MAX));
+    if (erc)
+        return erc;
 
     // A2-A4: MIN walk over every prefix
     WalkArgs a;
@@ -382,7 +497,6 @@ int solve_one(const void *Q, bool host_q, int n, int dtype, const qbf_options *o
     a.nitems = (npref + 31) / 32;
     a.ctr = ctr;
     a.pmin = pmin;
-    cudaEvent_t ev[2] = {nullptr, nullptr};
     if (o.timing) {
         QBF_CUDA(cudaEventCreate(&ev[0]), "cudaEventCreate");
         QBF_CUDA(cudaEventCreate(&ev[1]), "cudaEventCreate");
@@ -419,7 +533,6 @@ int solve_one(const void *Q, bool host_q, int n, int dtype, const qbf_options *o
     // A5-A7: threshold, flags, re-walk of flagged prefixes, rescoring, selection
     threshold_kernel<<<1, 1024, 0, s>>>(plan, pmin, npref, o.top_k, ctr);
     QBF_CUDA(cudaGetLastError(), "threshold_kernel");
-    const bool is_int = (dtype == QBF_I32 || dtype == QBF_I16);
     // With exact values (W = 0: integer Q, or an all-zero float Q) and
     // top_k = 1 the kernels re-walk only the lowest flagged prefix; they read
     // W from the plan, so the host sizes the grid for the general case.
@@ -446,10 +559,36 @@ int solve_one(const void *Q, bool host_q, int n, int dtype, const qbf_options *o
     select_kernel<<<1, 1024, 0, s>>>(plan, cand, vals, ctr, kCandCap, o.top_k, dres);
     QBF_CUDA(cudaGetLastError(), "select_kernel");
 
-    char *h = (char *)P->host;
     QBF_CUDA(cudaMemcpyAsync(h, dres, sizeof(DevResult), cudaMemcpyDeviceToHost, s), "copy result");
     QBF_CUDA(cudaMemcpyAsync(h + sizeof(DevResult), plan, offsetof(Plan, lin), cudaMemcpyDeviceToHost, s),
              "copy plan");
+    QBF_CUDA(cudaMemcpyAsync(h + sizeof(DevResult) + sizeof(Plan), &ctr->status, sizeof(int),
+                             cudaMemcpyDeviceToHost, s),
+             "copy status");
+    return QBF_OK;
+    };
+    // A repeated solve of the same device matrix with the same options replays
+    // a captured graph of the attempt (one launch instead of about a dozen);
+    // a first sighting runs directly, which also loads every kernel it uses
+    if (!host_q && !o.timing && graphs_enabled()) {
+        SolveKey key;
+        memset(&key, 0, sizeof(key));
+        key.Q = Q;
+        key.n = n;
+        key.dtype = dtype;
+        key.top_k = o.top_k;
+        key.variant = o.variant;
+        key.prefix_bits = o.prefix_bits;
+        key.fix_bits = o.fix_bits;
+        key.fix_value = o.fix_value;
+        key.dev = P->dev;
+        key.host = P->host;
+        key.total = L.total;
+        if ((rc = run_cached(key, enqueue, s)))
+            return rc;
+    } else if ((rc = enqueue(s))) {
+        return rc;
+    }
     QBF_CUDA(cudaStreamSynchronize(s), "solve");
     float walk_ms = 0.f;
     if (o.timing) {
@@ -471,7 +610,7 @@ int solve_one(const void *Q, bool host_q, int n, int dtype, const qbf_options *o
     }
     {
         int st = 0;
-        QBF_CUDA(cudaMemcpy(&st, &ctr->status, sizeof(int), cudaMemcpyDeviceToHost), "status");
+        memcpy(&st, h + sizeof(DevResult) + sizeof(Plan), sizeof(int));
         if (st != QBF_OK)
             return set_err(QBF_ECUDA, "a device-side wait ran out (tensor-core pipeline)");
     }
@@ -1100,6 +1239,7 @@ int qbf_release(void)
     release_batched();
     release_logz();
     std::lock_guard<std::mutex> lk(g_mu);
+    release_graphs();
     int cur = 0;
     cudaGetDevice(&cur);
     for (size_t d = 0; d < g_pools.size(); ++d) {
