@@ -28,6 +28,13 @@
  *    for that stream before returning.
  *  - The library keeps a per-device scratch pool (grow-only, reused across
  *    calls, freed by qbf_release).  Calls are serialised by an internal lock.
+ *  - qbf_solve of a device matrix with options and a pool seen before (the
+ *    second and later identical calls) replays a CUDA graph of the solve
+ *    captured at its second sighting; the kernels read Q when the graph runs,
+ *    so new contents in the same buffer are solved afresh.  Eight such solves
+ *    are remembered per device; setting the environment variable
+ *    QBF_NO_SOLVE_GRAPHS=1 runs every solve directly.  Solves with
+ *    opt->timing set, or with Q in host memory, always run directly.
  */
 #ifndef QBF_H
 #define QBF_H
