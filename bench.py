@@ -377,7 +377,7 @@ def run_profile_logz(count):
 
 ALU_OPS = ["IADD3", "IMNMX", "3-input integer min", "FADD", "FFMA", "FMNMX", "3-input FMNMX",
            "packed FADD (f32x2)", "IADD3 + IMNMX pair", "FADD + FMNMX pair", "EX2 (ex2.approx)",
-           "DADD (FP64)", "IMAD", "I2F + F2I pair"]
+           "DADD (FP64)", "IMAD", "I2F + F2I pair", "deferred-walk step mix (value-ops)"]
 
 
 def run_alu_microbench():

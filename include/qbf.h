@@ -517,7 +517,10 @@ int qbf_tc_selftest(const uint16_t *A_host, const uint16_t *B_host, float *D_hos
  *     6 3-input FMNMX, 7 packed FADD (f32x2), 8 IADD3+IMNMX pair,
  *     9 FADD+FMNMX pair, 10 ex2.approx (exponential unit), 11 FP64 add,
  *     12 integer multiply-add, 13 int32 -> FP32 -> int32 conversion pair
- *     (each conversion counts one).  Operations are counted as written in PTX:
+ *     (each conversion counts one), 14 the step mix of the table-driven
+ *     deferred walk without memory traffic (value-ops: 2 per state, at the
+ *     walk's launch shape; the ceiling of that instruction mix).
+ *     Operations are counted as written in PTX:
  *     the assembler may merge consecutive dependent two-input mins.
  * Writes scalar lane operations per SM clock per SM to *ops_per_clk_sm (a
  * packed f32x2 add counts two, each instruction of a pair counts one), the

@@ -1115,8 +1115,8 @@ int qbf_alu_microbench(int op, double *ops_per_clk_sm, double *sm_mhz, double *s
 {
     if (!ops_per_clk_sm || !sm_mhz || !seconds)
         return set_err(QBF_EINVAL, "null pointer argument");
-    if (op < 0 || op > 13)
-        return set_err(QBF_EINVAL, "op must be in [0, 13]");
+    if (op < 0 || op > 14)
+        return set_err(QBF_EINVAL, "op must be in [0, 14]");
     std::lock_guard<std::mutex> lk(g_mu);
     cudaError_t e = run_alu_microbench(op, ops_per_clk_sm, sm_mhz, seconds, (cudaStream_t)stream);
     if (e != cudaSuccess)

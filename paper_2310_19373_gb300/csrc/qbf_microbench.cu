@@ -4,7 +4,10 @@
 // denominator is the number of lane operations an SM retires per clock.
 // Each kernel below runs 8 independent dependency chains per thread of one
 // instruction class, fills every SM with one wave of resident blocks, and is
-// timed with CUDA events.  The result is lane operations per SM clock per SM
+// timed with CUDA events and with the blocks' SM cycle counters (read after a
+// barrier: warps of one block finish far apart, the first ones early, so a
+// single warp's count understates the block's time).  The result is lane
+// operations per SM clock per SM
 // (a packed f32x2 add counts as two; each instruction of a pair counts one).
 // The figures count the operations written in PTX: the assembler may merge two
 // consecutive dependent mins of a chain into one three-input min, so the
@@ -13,6 +16,7 @@
 // cycles, per ncu).  Ops 10-13 (the exponential unit, FP64 add, integer
 // multiply-add, int/float conversions) serve the log Z and rescoring rooflines.
 #include <cstdint>
+#include <cstring>
 #include <vector>
 
 #include "qbf_kernels.cuh"
@@ -81,6 +85,7 @@ __global__ void __launch_bounds__(kMbThreads) alu_kernel(int iters, unsigned see
             }
         }
     }
+    __syncthreads();  // the block's time, not its first warp's
     const long long t1 = clock64();
     unsigned acc = 0;
     for (int j = 0; j < 8; ++j)
@@ -90,6 +95,183 @@ __global__ void __launch_bounds__(kMbThreads) alu_kernel(int iters, unsigned see
         sink[0] = acc;
     if (threadIdx.x == 0)
         cycles[blockIdx.x] = t1 - t0;
+}
+
+// Op 14: the step of the table-driven deferred walk with no global memory
+// traffic -- per step and thread 4 packed adds of field pairs, the eight-value
+// min tree, and per two steps one packed add of an F pair read from shared
+// memory and a three-input min into a running minimum -- at the walk's launch
+// shape (256 threads, three CTAs per SM).  Its rate is the ceiling of that
+// instruction mix on this part, against which the walk's own rate (with its
+// block transitions, table staging and per-prefix set-up) is compared.
+constexpr int kMixThreads = 256;
+__device__ __forceinline__ unsigned long long mx_add(unsigned long long a, unsigned long long b)
+{
+    unsigned long long r;
+    asm("add.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(a), "l"(b));
+    return r;
+}
+__device__ __forceinline__ unsigned long long mx_sub(unsigned long long a, unsigned long long b)
+{
+    unsigned long long r;
+    asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(a), "l"(b));
+    return r;
+}
+__device__ __forceinline__ unsigned long long mx_pack(float a, float b)
+{
+    unsigned long long r;
+    asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(a), "f"(b));
+    return r;
+}
+__device__ __forceinline__ void mx_unpack(unsigned long long v, float &a, float &b)
+{
+    asm("mov.b64 {%0, %1}, %2;" : "=f"(a), "=f"(b) : "l"(v));
+}
+__device__ __forceinline__ float mx_min3(float a, float b, float c)
+{
+    float r;
+    asm("min.f32 %0, %1, %2, %3;" : "=f"(r) : "f"(a), "f"(b), "f"(c));
+    return r;
+}
+__device__ __forceinline__ unsigned long long mx_lds(const unsigned long long *p)
+{
+    unsigned long long r;  // volatile: one load per use, as in the walk
+    asm volatile("ld.shared.u64 %0, [%1];" : "=l"(r) : "r"((unsigned)__cvta_generic_to_shared(p)));
+    return r;
+}
+__host__ __device__ constexpr int mx_ctz(int u)
+{
+    int l = 0;
+    while (!((u >> l) & 1))
+        ++l;
+    return l;
+}
+
+__global__ void __launch_bounds__(kMixThreads, 3)
+    step_mix_kernel(int blocks, const unsigned long long *init, unsigned *sink, long long *cycles)
+{
+    __shared__ __align__(16) unsigned long long sF[kMixThreads / 32][32];
+    unsigned long long w[4], GF[4][6];
+    float m0 = 3e38f, m1 = 3e38f;
+    const int b = (threadIdx.x & 63) * 32;
+#pragma unroll
+    for (int s = 0; s < 4; ++s) {
+        w[s] = init[b + s];
+#pragma unroll
+        for (int l = 0; l < 6; ++l)
+            GF[s][l] = init[b + 4 + s * 6 + l];
+    }
+    sF[threadIdx.x >> 5][threadIdx.x & 31] = init[b + (threadIdx.x & 31)];
+    __syncwarp();
+    const unsigned long long *Fs = sF[threadIdx.x >> 5];
+    const long long t0 = clock64();
+    for (int B = 0; B < blocks; ++B) {
+        float tp = 0.f;
+#pragma unroll
+        for (int u = 0; u < 64; ++u) {
+            if (u > 0) {
+                const int l = mx_ctz(u);
+                const int nb = ((u ^ (u >> 1)) >> l) & 1;
+#pragma unroll
+                for (int s = 0; s < 4; ++s)
+                    w[s] = (nb ^ (l == 5 ? (B & 1) : 0)) ? mx_add(w[s], GF[s][l])
+                                                         : mx_sub(w[s], GF[s][l]);
+            }
+            float x[8];
+#pragma unroll
+            for (int s = 0; s < 4; ++s)
+                mx_unpack(w[s], x[2 * s], x[2 * s + 1]);
+            const float a = mx_min3(x[0], x[1], x[2]), c3 = mx_min3(x[3], x[4], x[5]);
+            const float t = fminf(c3, mx_min3(x[6], x[7], a));
+            if (u & 1) {
+                const unsigned long long y = mx_add(mx_pack(tp, t), mx_lds(Fs + ((u >> 1) & 31)));
+                float lo, hi;
+                mx_unpack(y, lo, hi);
+                if ((u >> 1) & 1)
+                    m1 = mx_min3(m1, lo, hi);
+                else
+                    m0 = mx_min3(m0, lo, hi);
+            } else {
+                tp = t;
+            }
+        }
+    }
+    __syncthreads();  // the block's time, not its first warp's
+    const long long t1 = clock64();
+    if (__float_as_uint(fminf(m0, m1)) == 0x12345678u)
+        sink[0] = 1;
+    if (threadIdx.x == 0)
+        cycles[blockIdx.x] = t1 - t0;
+}
+
+cudaError_t run_step_mix(double *value_ops_per_clk_sm, double *sm_mhz, double *seconds,
+                         cudaStream_t s)
+{
+    int dev = 0, nsm = 0, bps = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess)
+        return e;
+    if ((e = cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess)
+        return e;
+    if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, step_mix_kernel, kMixThreads,
+                                                           0)) != cudaSuccess)
+        return e;
+    if (bps < 1)
+        bps = 1;
+    const int grid = nsm * bps, blocks = 2048;
+    unsigned *sink = nullptr;
+    long long *cyc = nullptr;
+    unsigned long long *init = nullptr;
+    std::vector<unsigned long long> h_init(64 * 32);
+    for (size_t i = 0; i < h_init.size(); ++i) {
+        const float a = (float)(i % 97), c = (float)(i % 89);
+        unsigned ua, uc;
+        memcpy(&ua, &a, 4);
+        memcpy(&uc, &c, 4);
+        h_init[i] = ((unsigned long long)uc << 32) | ua;
+    }
+    if ((e = cudaMalloc(&sink, sizeof(unsigned))) != cudaSuccess)
+        return e;
+    if ((e = cudaMalloc(&cyc, sizeof(long long) * grid)) == cudaSuccess &&
+        (e = cudaMalloc(&init, sizeof(unsigned long long) * h_init.size())) == cudaSuccess)
+        e = cudaMemcpy(init, h_init.data(), sizeof(unsigned long long) * h_init.size(),
+                       cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) {
+        cudaFree(sink);
+        cudaFree(cyc);
+        cudaFree(init);
+        return e;
+    }
+    cudaEvent_t ev0, ev1;
+    cudaEventCreate(&ev0);
+    cudaEventCreate(&ev1);
+    step_mix_kernel<<<grid, kMixThreads, 0, s>>>(4, init, sink, cyc);  // warm-up
+    cudaEventRecord(ev0, s);
+    step_mix_kernel<<<grid, kMixThreads, 0, s>>>(blocks, init, sink, cyc);
+    cudaEventRecord(ev1, s);
+    e = cudaEventSynchronize(ev1);
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, ev0, ev1);
+    std::vector<long long> h(grid);
+    if (e == cudaSuccess)
+        e = cudaMemcpy(h.data(), cyc, sizeof(long long) * grid, cudaMemcpyDeviceToHost);
+    cudaEventDestroy(ev0);
+    cudaEventDestroy(ev1);
+    cudaFree(sink);
+    cudaFree(cyc);
+    cudaFree(init);
+    if (e != cudaSuccess)
+        return e;
+    double mean_cyc = 0;
+    for (long long c : h)
+        mean_cyc += (double)c;
+    mean_cyc /= grid;
+    // 8 states per thread and step, 2 value-ops per state
+    const double ops_per_sm = (double)blocks * 64 * 8 * 2 * kMixThreads * bps;
+    *value_ops_per_clk_sm = ops_per_sm / mean_cyc;
+    *seconds = ms * 1e-3;
+    *sm_mhz = mean_cyc / (ms * 1e-3) * 1e-6;
+    return cudaSuccess;
 }
 
 template <int OP>
@@ -169,6 +351,7 @@ cudaError_t run_alu_microbench(int op, double *ops_per_clk_sm, double *sm_mhz, d
     case 11: return run_op<11>(iters / 16, ops_per_clk_sm, sm_mhz, seconds, s);
     case 12: return run_op<12>(iters, ops_per_clk_sm, sm_mhz, seconds, s);
     case 13: return run_op<13>(iters / 4, ops_per_clk_sm, sm_mhz, seconds, s);
+    case 14: return run_step_mix(ops_per_clk_sm, sm_mhz, seconds, s);
     default: return cudaErrorInvalidValue;
     }
 }

@@ -118,7 +118,8 @@ __global__ void __launch_bounds__(kWalkThreads, 3)
 // running minimum.  |w| and |F| stay below 2^23, so every operation is exact.
 // ---------------------------------------------------------------------------
 
-constexpr int kDefer2MaxM = 14;  // largest 2^M blocks of 2^R states per lane (table <= 4 MB)
+constexpr int kDefer2R = 7;      // low bits per block: 128 unrolled steps per block
+constexpr int kDefer2MaxM = 14;  // largest 2^M blocks of 2^R states per lane (table <= 8 MB)
 constexpr int kDefer2Threads = 256;
 constexpr int kDefer2CtasPerSm = 3;  // at most 80 registers
 
@@ -143,18 +144,20 @@ __global__ void defer2_ftab_kernel(const Plan *__restrict__ plan, int nsw, float
 
 
 // The table-driven MIN walk: same geometry, groups and output as
-// walk_defer_min_kernel (a.ns = nsw + 3), R = kRMax.
+// walk_defer_min_kernel (a.ns = nsw + 3), with blocks of 2^kDefer2R states
+// (one more unrolled bit than the record-driven walk: the block transitions
+// cost half as much per state, and the table needs no records).
 __global__ void __launch_bounds__(kDefer2Threads, kDefer2CtasPerSm)
     walk_defer2_min_kernel(const Plan *__restrict__ plan, const float *__restrict__ ftab, WalkArgs a)
 {
-    constexpr int R = kRMax;
+    constexpr int R = kDefer2R;
     extern __shared__ __align__(16) int smem[];
     const int n = a.n;
     const int nsg = a.ns;
     const int nsw = nsg - 3;
     const int nmid = nsw - R;
-    float *fbufs = reinterpret_cast<float *>(smem);  // per warp: two blocks of 64 F values
-    ulonglong2 *sGFx = reinterpret_cast<ulonglong2 *>(fbufs + (kDefer2Threads / 32) * 128);
+    float *fbufs = reinterpret_cast<float *>(smem);  // per warp: two blocks of 2^R F values
+    ulonglong2 *sGFx = reinterpret_cast<ulonglong2 *>(fbufs + (kDefer2Threads / 32) * (2 << R));
     float4 *sE = reinterpret_cast<float4 *>(sGFx + (R - kDefer2RegBits) * 2 * kDefer2Threads);
     float *sCf = reinterpret_cast<float *>(sE + nmid * 4);
     int *sS = reinterpret_cast<int *>(sCf + nmid * kDefer2Threads);
@@ -178,7 +181,7 @@ __global__ void __launch_bounds__(kDefer2Threads, kDefer2CtasPerSm)
     if (plan->status != QBF_OK)
         return;
     const int lane = threadIdx.x & 31;
-    float *fbuf = fbufs + (threadIdx.x >> 5) * 128;
+    float *fbuf = fbufs + (threadIdx.x >> 5) * (2 << R);
     const int stride = blockDim.x, slot = threadIdx.x;
     while (true) {
         unsigned long long item = 0;
@@ -206,7 +209,7 @@ __global__ void __launch_bounds__(kDefer2Threads, kDefer2CtasPerSm)
 
 size_t walk_defer_table_floats(int R, int nsw)
 {
-    if (R != kRMax || nsw < R || nsw - R > kDefer2MaxM)
+    if (R != kRMax || nsw < kDefer2R || nsw - kDefer2R > kDefer2MaxM)
         return 0;
     return (size_t)1 << nsw;
 }
@@ -221,9 +224,9 @@ static cudaError_t launch_defer2(const Plan *plan, float *ftab, const WalkArgs &
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess)
         return e;
-    const int nmid = nsw - kRMax;
-    const size_t smem = sizeof(float) * (kDefer2Threads / 32) * 128 +
-                        sizeof(ulonglong2) * (kRMax - kDefer2RegBits) * 2 * kDefer2Threads +
+    const int nmid = nsw - kDefer2R;
+    const size_t smem = sizeof(float) * (kDefer2Threads / 32) * (2 << kDefer2R) +
+                        sizeof(ulonglong2) * (kDefer2R - kDefer2RegBits) * 2 * kDefer2Threads +
                         sizeof(float4) * nmid * 4 +
                         sizeof(float) * nmid * kDefer2Threads + sizeof(int) * (a.n * a.n + a.n);
     auto k = walk_defer2_min_kernel;

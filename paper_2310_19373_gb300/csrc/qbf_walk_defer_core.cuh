@@ -242,8 +242,10 @@ __device__ __forceinline__ int walk_min_rt(Lane<R> &L, int n, int nsg, const int
 
 // low-bit fields kept in registers; those of variables kDefer2RegBits..R-1
 // (flipped 2^(R-1-l) times per block) are read from the lane's shared memory.
-// Measured at n = 40: all six in registers 54.5 ms; five 57.2 ms; four 57.1 ms
-// (three CTAs per SM), 58.6 ms (four CTAs per SM, 64 registers with spills).
+// Measured at n = 40 with 64-step blocks: all six in registers 54.5 ms; five
+// 57.2 ms; four 57.1 ms (three CTAs per SM), 58.6 ms (four CTAs per SM, 64
+// registers with spills).  With 128-step blocks the seventh (flipped once per
+// block) comes from shared memory: 53.0 ms.
 constexpr int kDefer2RegBits = 6;
 
 namespace dfr2 {
@@ -437,10 +439,10 @@ __device__ __forceinline__ int walk_min(Lane<R> &L, int nsw, const float *ftab, 
         cp16(fbuf + 4 * lane, ftab + 4 * lane);
     cp_commit();
     for (unsigned B = 0; B < nblocks; ++B) {
-        const float *cur = fbuf + (B & 1) * 64;
+        const float *cur = fbuf + (B & 1) * BS;
         if (B + 1 < nblocks) {
             if (lane < BS / 4)
-                cp16(fbuf + ((B + 1) & 1) * 64 + 4 * lane, ftab + (size_t)(B + 1) * BS + 4 * lane);
+                cp16(fbuf + ((B + 1) & 1) * BS + 4 * lane, ftab + (size_t)(B + 1) * BS + 4 * lane);
             cp_commit();
             cp_wait<1>();
         } else {
