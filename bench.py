@@ -47,7 +47,7 @@ PIPE_LANES_PER_SM = 128 + 128
 WALK_KERNELS = {0: "walk_split_kernel<6, MIN>", 1: "field_min_kernel", 2: "walk_split_kernel<6, MIN>",
                 6: "naive_min_kernel",
                 3: "tc_min_kernel", 4: "walk_f32x2_min_kernel<6>", 5: "walk_mix_min_kernel<6>",
-                7: "walk_defer2_min_kernel"}
+                7: "walk_defer2_min_kernel<7>"}
 
 
 def env_int(name, default):

@@ -118,8 +118,13 @@ __global__ void __launch_bounds__(kWalkThreads, 3)
 // running minimum.  |w| and |F| stay below 2^23, so every operation is exact.
 // ---------------------------------------------------------------------------
 
-constexpr int kDefer2R = 7;      // low bits per block: 128 unrolled steps per block
-constexpr int kDefer2MaxM = 14;  // largest 2^M blocks of 2^R states per lane (table <= 8 MB)
+// Low bits per block (unrolled steps 2^R): 7 for long lane walks, where
+// 128-step blocks halve the transition cost per state (n = 40: 53.0 against
+// 54.5 ms), 6 for short ones, where the shorter code and set-up win (n = 32,
+// 2^10 steps per lane: 0.297 against 0.311 ms).
+constexpr int kDefer2LongR = 7;
+constexpr int kDefer2LongNsw = 14;  // lane walks of at least 2^14 steps take R = 7
+constexpr int kDefer2MaxM = 14;     // largest 2^M blocks of 2^R states per lane (table <= 8 MB)
 constexpr int kDefer2Threads = 256;
 constexpr int kDefer2CtasPerSm = 3;  // at most 80 registers
 
@@ -144,13 +149,13 @@ __global__ void defer2_ftab_kernel(const Plan *__restrict__ plan, int nsw, float
 
 
 // The table-driven MIN walk: same geometry, groups and output as
-// walk_defer_min_kernel (a.ns = nsw + 3), with blocks of 2^kDefer2R states
+// walk_defer_min_kernel (a.ns = nsw + 3), with blocks of 2^R states
 // (one more unrolled bit than the record-driven walk: the block transitions
 // cost half as much per state, and the table needs no records).
+template <int R>
 __global__ void __launch_bounds__(kDefer2Threads, kDefer2CtasPerSm)
     walk_defer2_min_kernel(const Plan *__restrict__ plan, const float *__restrict__ ftab, WalkArgs a)
 {
-    constexpr int R = kDefer2R;
     extern __shared__ __align__(16) int smem[];
     const int n = a.n;
     const int nsg = a.ns;
@@ -209,11 +214,12 @@ __global__ void __launch_bounds__(kDefer2Threads, kDefer2CtasPerSm)
 
 size_t walk_defer_table_floats(int R, int nsw)
 {
-    if (R != kRMax || nsw < kDefer2R || nsw - kDefer2R > kDefer2MaxM)
+    if (R != kRMax || nsw < kRMax || nsw - (nsw >= kDefer2LongNsw ? kDefer2LongR : kRMax) > kDefer2MaxM)
         return 0;
     return (size_t)1 << nsw;
 }
 
+template <int R>
 static cudaError_t launch_defer2(const Plan *plan, float *ftab, const WalkArgs &a, int num_sms,
                                  cudaStream_t s)
 {
@@ -224,12 +230,12 @@ static cudaError_t launch_defer2(const Plan *plan, float *ftab, const WalkArgs &
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess)
         return e;
-    const int nmid = nsw - kDefer2R;
-    const size_t smem = sizeof(float) * (kDefer2Threads / 32) * (2 << kDefer2R) +
-                        sizeof(ulonglong2) * (kDefer2R - kDefer2RegBits) * 2 * kDefer2Threads +
+    const int nmid = nsw - R;
+    const size_t smem = sizeof(float) * (kDefer2Threads / 32) * (2 << R) +
+                        sizeof(ulonglong2) * (R - kDefer2RegBits) * 2 * kDefer2Threads +
                         sizeof(float4) * nmid * 4 +
                         sizeof(float) * nmid * kDefer2Threads + sizeof(int) * (a.n * a.n + a.n);
-    auto k = walk_defer2_min_kernel;
+    auto k = walk_defer2_min_kernel<R>;
     e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess)
         return e;
@@ -307,7 +313,9 @@ cudaError_t launch_walk_defer(int R, const Plan *plan, const Rec *recs, const Wa
     if (R < 1 || R > kRMax)
         return cudaErrorInvalidValue;
     if (ftab_dev && walk_defer_table_floats(R, a.ns - 3) > 0)
-        return launch_defer2(plan, ftab_dev, a, num_sms, s);
+        return a.ns - 3 >= kDefer2LongNsw
+                   ? launch_defer2<kDefer2LongR>(plan, ftab_dev, a, num_sms, s)
+                   : launch_defer2<kRMax>(plan, ftab_dev, a, num_sms, s);
     float *tab = static_cast<float *>(scratch_dev);  // 130 floats
     k_defer_tables_kernel<<<1, 32, 0, s>>>(Kbuf_dev, R, tab);
     cudaError_t e = cudaGetLastError();

@@ -1,7 +1,8 @@
 """Per-prefix parity at the full walk depth of the n = 40 solve.
 
-A certified n = 40 solve walks 16 suffix bits per lane (blocks of 2^6 states,
-block-transition records at levels 6..15) for 2^21 prefixes.  Walking all of
+A certified n = 40 solve walks 16 suffix bits per lane for 2^21 prefixes: the
+table-driven deferred walk in blocks of 2^7 states (mid-bit flips at levels
+7..15), the record-driven walks in blocks of 2^6 (records at levels 6..15).  Walking all of
 them against the oracle is too slow for a test, so qbf_prefix_minima_fixed
 runs the production MIN kernel in exactly that geometry over windows of 2^11
 prefixes (the top prefix variables fixed), and every prefix's minimum of the
@@ -38,13 +39,18 @@ def fixed_point_image(Q, sigma):
 
 # (variant, prefix_bits of the automatic n = 40 geometry): suffix = 19 for the
 # eight-prefix walks (16 walked + 3 group bits), 17 for the packed pair walk
-# (16 + 1 pair bit), 16 for the int32 walk, 14 (one tile) for the tensor-core form
+# (16 + 1 pair bit), 16 for the int32 walk, 14 (one tile) for the tensor-core form;
+# and the table-driven deferred walk at the two lane depths around its switch
+# from 128-step to 64-step blocks (14 walked bits: 2^7 blocks of 128; 13: 2^7
+# blocks of 64)
 FORMS = [(qb.QBF_VARIANT_SPLIT_DEFER, 21), (qb.QBF_VARIANT_SPLIT_MIX, 21),
-         (qb.QBF_VARIANT_SPLIT_F32, 23), (qb.QBF_VARIANT_SPLIT, 24), (qb.QBF_VARIANT_TC, 26)]
+         (qb.QBF_VARIANT_SPLIT_F32, 23), (qb.QBF_VARIANT_SPLIT, 24), (qb.QBF_VARIANT_TC, 26),
+         (qb.QBF_VARIANT_SPLIT_DEFER, 23), (qb.QBF_VARIANT_SPLIT_DEFER, 24)]
 WINDOW = 11  # prefixes per window: 2^11
 
 
-@pytest.mark.parametrize("variant,k", FORMS, ids=["defer", "mix", "f32", "split", "tc"])
+@pytest.mark.parametrize("variant,k", FORMS,
+                         ids=["defer", "mix", "f32", "split", "tc", "defer-14", "defer-13"])
 def test_n40_prefix_minima_at_full_depth(variant, k):
     n = 40
     Q = inputs.config_n40_f32(0)
