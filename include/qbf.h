@@ -317,6 +317,37 @@ int qbf_solve_batched_info(const void *const *Q_dev, const int *n, const int *dt
                            qbf_batch_info *info, void *stream);
 
 /*
+ * qbf_solve_batched_item_minima -- the batched MIN walk's per-item minima of
+ * one instance, for checking the walk against a reference at its own depth.
+ *
+ * Runs the same work as qbf_solve_batched_info (same arguments; `info` may be
+ * NULL) and then copies out what the MIN pass wrote for instance `inst`
+ * (0 <= inst < count).  The batch walks Section 3.1's split: instance i has
+ * 2^p prefixes, p = info[i].prefix_bits, each walked over its 2^s suffix
+ * states, s = info[i].suffix_bits.  The work items are runs of 32 prefixes,
+ * and item j of the instance covers the natural indices
+ * [32 j 2^s, (32 j + 32) 2^s) ∩ [0, 2^n).  item_min[j] is the minimum over
+ * those states of f on the walk's fixed-point image:
+ *   - the diagonal is round(Q_ii 2^sigma);
+ *   - each pair i < j adds round((Q_ij + Q_ji) 2^sigma);
+ *   - sigma = info[inst].scale_bits, and rounding is half to even;
+ *   - the value is an int32.
+ * Instances with n below 11 are walked padded to n = 11 with zero rows, so
+ * their items cover the padded space.
+ *
+ * item_min : host array of max_items entries (may be NULL if max_items = 0);
+ *            the first min(max_items, count of items) are written.
+ * n_items  : receives the instance's item count, ceil(2^p / 32).
+ * With QBF_VARIANT_AUTO the minima are those of the pass that answered: the
+ * int32 pass when the FP32 windows overflowed.  Errors as qbf_solve_batched,
+ * plus QBF_EINVAL for inst out of range or a null n_items.
+ */
+int qbf_solve_batched_item_minima(const void *const *Q_dev, const int *n, const int *dtype,
+                                  int count, const qbf_options *opt, int inst, int32_t *item_min,
+                                  uint64_t max_items, uint64_t *n_items, qbf_batch_info *info,
+                                  void *stream);
+
+/*
  * qbf_tune -- autotuner of the batched solver, per n and element class.
  *
  * For every n in [n_min, n_max] (1 <= n_min <= n_max <= QBF_BATCH_MAX_N) it

@@ -141,6 +141,14 @@ _SIGS = {
                                               ctypes.POINTER(ctypes.c_double),
                                               ctypes.POINTER(ctypes.c_uint64),
                                               ctypes.POINTER(QbfBatchInfo), _VP]),
+    "qbf_solve_batched_item_minima": (ctypes.c_int, [ctypes.POINTER(ctypes.c_void_p),
+                                                     ctypes.POINTER(ctypes.c_int),
+                                                     ctypes.POINTER(ctypes.c_int), ctypes.c_int,
+                                                     ctypes.POINTER(QbfOptions), ctypes.c_int,
+                                                     ctypes.POINTER(ctypes.c_int32),
+                                                     ctypes.c_uint64,
+                                                     ctypes.POINTER(ctypes.c_uint64),
+                                                     ctypes.POINTER(QbfBatchInfo), _VP]),
     "qbf_tune": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_char_p]),
     "qbf_tuned_params": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.POINTER(ctypes.c_int),
                                         ctypes.POINTER(ctypes.c_int)]),
@@ -310,6 +318,37 @@ def qbf_solve_batched_info(Q_ptrs, ns, dtypes, opt: QbfOptions | None,
                                       info, _VP(stream or 0))
     _check(rc)
     return list(vmin), [int(v) for v in am], list(info)
+
+
+def qbf_solve_batched_item_minima(Q_ptrs, ns, dtypes, opt: QbfOptions | None, inst: int,
+                                  max_items: int, stream: int | None = None):
+    """Per-item minima of instance `inst` (items of 32 prefixes) and the batch's
+    QbfBatchInfo list; see include/qbf.h."""
+    count, P, N, D = _batch_arrays(Q_ptrs, ns, dtypes)
+    out = (ctypes.c_int32 * max(1, max_items))()
+    nit = ctypes.c_uint64()
+    info = (QbfBatchInfo * count)()
+    rc = lib().qbf_solve_batched_item_minima(P, N, D, count,
+                                             ctypes.byref(opt) if opt is not None else None,
+                                             inst, out, max_items, ctypes.byref(nit), info,
+                                             _VP(stream or 0))
+    _check(rc)
+    return list(out[:min(max_items, nit.value)]), nit.value, list(info)
+
+
+def batched_item_minima(Qs, inst: int, max_items: int, batch_suffix_bits: int = 0,
+                        stream=None, variant: int = QBF_VARIANT_AUTO):
+    """Per-item minima of instance `inst` of a batched solve of square CUDA
+    tensors: (item minima, item count, per-instance QbfBatchInfo)."""
+    import torch
+
+    Qs = [q.contiguous() for q in Qs]
+    opt = qbf_default_options()
+    opt.batch_suffix_bits = batch_suffix_bits
+    opt.variant = variant
+    s = stream if stream is not None else torch.cuda.current_stream().cuda_stream
+    return qbf_solve_batched_item_minima([q.data_ptr() for q in Qs], [q.shape[0] for q in Qs],
+                                         [dtype_code(q) for q in Qs], opt, inst, max_items, s)
 
 
 def qbf_tune(n_min: int, n_max: int, dtype: int, cache_path: str | None = None) -> None:

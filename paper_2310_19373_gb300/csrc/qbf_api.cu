@@ -1139,6 +1139,25 @@ int qbf_solve_batched_info(const void *const *Q_dev, const int *n, const int *dt
                          nullptr, info, 0);
 }
 
+int qbf_solve_batched_item_minima(const void *const *Q_dev, const int *n, const int *dtype,
+                                  int count, const qbf_options *opt, int inst, int32_t *item_min,
+                                  uint64_t max_items, uint64_t *n_items, qbf_batch_info *info,
+                                  void *stream)
+{
+    if (!n_items)
+        return set_err(QBF_EINVAL, "n_items must not be null");
+    if (count < 1 || count > QBF_BATCH_MAX_COUNT)
+        return set_err(QBF_EINVAL, "count must be in [1, 65536]");
+    std::vector<double> vmin(count);
+    std::vector<uint64_t> am(count);
+    unsigned long long ni = 0;
+    const BatchItemsOut out{inst, item_min, (unsigned long long)max_items, &ni};
+    const int rc = solve_batched(Q_dev, n, dtype, count, opt, vmin.data(), am.data(),
+                                 (cudaStream_t)stream, nullptr, info, 0, &out);
+    *n_items = ni;
+    return rc;
+}
+
 int qbf_tune(int n_min, int n_max, int dtype, const char *cache_path)
 {
     return tune_batched_table(n_min, n_max, dtype, cache_path);

@@ -715,7 +715,7 @@ int dtsize(int dt)
 int solve_batched_mode(const void *const *Q, const int *n, const int *dtype, int count,
                        const qbf_options *opt_in, double *min_value, uint64_t *argmin,
                        cudaStream_t s, int *kernel_launches, int mix, qbf_batch_info *info_out,
-                       int ctas_override)
+                       int ctas_override, const BatchItemsOut *items_out)
 {
     if (!Q || !n || !dtype || !min_value || !argmin)
         return record_error(QBF_EINVAL, "null pointer argument");
@@ -729,6 +729,10 @@ int solve_batched_mode(const void *const *Q, const int *n, const int *dtype, int
         return record_error(QBF_ENOTIMPL, "qbf_solve_batched returns the minimum only (top_k = 1)");
     if (o.fix_bits != 0)
         return record_error(QBF_ENOTIMPL, "qbf_solve_batched does not restrict the space");
+    if (items_out && (items_out->inst < 0 || items_out->inst >= count || !items_out->n_items ||
+                      (items_out->max_items > 0 && !items_out->item_min)))
+        return record_error(QBF_EINVAL, "item minima: inst must be in [0, count) and the "
+                                        "output pointers non-null");
     std::lock_guard<std::mutex> lk(g_bmu);
     int dev = 0;
     B_CUDA(cudaGetDevice(&dev), "cudaGetDevice");
@@ -906,6 +910,17 @@ int solve_batched_mode(const void *const *Q, const int *n, const int *dtype, int
             info_out[i].walk = inf[i].walk;
         }
     }
+    if (items_out) {
+        const BatchDesc &d = desc[items_out->inst];
+        const unsigned long long ni = (d.nprefix + 31) / 32;
+        *items_out->n_items = ni;
+        const unsigned long long c = std::min(ni, items_out->max_items);
+        if (c > 0)
+            B_CUDA(cudaMemcpy(items_out->item_min, (const char *)B.dev + L.item_min +
+                                                       sizeof(int) * d.item_off,
+                              sizeof(int) * c, cudaMemcpyDeviceToHost),
+                   "item minima");
+    }
     return QBF_OK;
 }
 
@@ -915,7 +930,8 @@ int solve_batched_mode(const void *const *Q, const int *n, const int *dtype, int
 // QBF_VARIANT_SPLIT: the int32 pass.
 int solve_batched(const void *const *Q, const int *n, const int *dtype, int count,
                   const qbf_options *opt_in, double *min_value, uint64_t *argmin,
-                  cudaStream_t s, int *kernel_launches, qbf_batch_info *info, int ctas_override)
+                  cudaStream_t s, int *kernel_launches, qbf_batch_info *info, int ctas_override,
+                  const BatchItemsOut *items_out)
 {
     const int variant = opt_in ? opt_in->variant : QBF_VARIANT_AUTO;
     if (variant != QBF_VARIANT_AUTO && variant != QBF_VARIANT_SPLIT &&
@@ -924,13 +940,13 @@ int solve_batched(const void *const *Q, const int *n, const int *dtype, int coun
                             "qbf_solve_batched runs the int32, two-pipe or deferred-correction walk");
     if (variant == QBF_VARIANT_SPLIT)
         return solve_batched_mode(Q, n, dtype, count, opt_in, min_value, argmin, s,
-                                  kernel_launches, 0, info, ctas_override);
+                                  kernel_launches, 0, info, ctas_override, items_out);
     const int rc = solve_batched_mode(Q, n, dtype, count, opt_in, min_value, argmin, s,
                                       kernel_launches, variant == QBF_VARIANT_SPLIT_MIX ? 1 : 2,
-                                      info, ctas_override);
+                                      info, ctas_override, items_out);
     if (rc == QBF_EOVERFLOW && variant == QBF_VARIANT_AUTO)
         return solve_batched_mode(Q, n, dtype, count, opt_in, min_value, argmin, s,
-                                  kernel_launches, 0, info, ctas_override);
+                                  kernel_launches, 0, info, ctas_override, items_out);
     return rc;
 }
 

@@ -66,9 +66,20 @@ __global__ void select_kernel(const Plan *plan, const unsigned long long *cand,
 int record_error(int code, const char *msg);
 
 // qbf_batched.cu
+// Where a batched solve copies the MIN pass's per-item minima of one instance
+// (item j: prefixes 32j..32j+31, the fixed-point image's minimum over their
+// states): at most max_items of them into item_min (host), their count into
+// *n_items.
+struct BatchItemsOut {
+    int inst;
+    int *item_min;
+    unsigned long long max_items;
+    unsigned long long *n_items;
+};
 int solve_batched(const void *const *Q, const int *n, const int *dtype, int count,
                   const qbf_options *opt, double *min_value, uint64_t *argmin, cudaStream_t s,
-                  int *kernel_launches, qbf_batch_info *info = nullptr, int ctas_override = 0);
+                  int *kernel_launches, qbf_batch_info *info = nullptr, int ctas_override = 0,
+                  const BatchItemsOut *items_out = nullptr);
 int set_tuned_batch_ns(int ns);
 int tune_batched_table(int n_min, int n_max, int dtype, const char *cache_path);
 int tuned_params(int n, int dtype, int *suffix_bits, int *ctas_per_sm);
