@@ -116,7 +116,7 @@ typedef struct {
                            `stream` and report it in qbf_result.walk_seconds */
     int batch_suffix_bits; /* qbf_solve_batched: suffix bits walked per lane,
                               6..18; 0 = the value qbf_tune chose for the
-                              instance's n (cache), else 16                 */
+                              instance's n (cache), else 18                 */
     int reserved[6];
 } qbf_options;
 
@@ -276,7 +276,7 @@ int qubo_bf_solve(const void *Q_host, int n, int dtype, double *min_value, uint6
  * n, dtype  : host arrays of `count` entries; 1 <= n[i] <= QBF_BATCH_MAX_N.
  * opt       : NULL or top_k = 1, fix_bits = 0; batch_suffix_bits selects the
  *             per-lane suffix width (0 = the qbf_tune choice for each
- *             instance's n, else 16; see qbf_tune and qbf_tune_batched);
+ *             instance's n, else 18; see qbf_tune and qbf_tune_batched);
  *             variant AUTO / SPLIT_DEFER (instances whose image fits 2^23
  *             walk in the deferred-correction form, the rest in int32; AUTO
  *             repeats the batch on the int32 walk after QBF_EOVERFLOW),
@@ -353,14 +353,16 @@ int qbf_solve_batched_item_minima(const void *const *Q_dev, const int *n, const 
  * For every n in [n_min, n_max] (1 <= n_min <= n_max <= QBF_BATCH_MAX_N) it
  * builds synthetic batches of that n on the current device (upper-triangular
  * instances, uniform in [-1, 1] for float dtypes, integers in [-50, 50] for
- * integer dtypes; c and 2c instances, c = 2^36 / 2^n, at most 2048) and
- * scores each configuration by the difference of their qbf_solve_batched
- * times: the steady-state cost of c instances, as in a large mixed batch,
- * without the last partial wave of one small launch.  It searches the suffix
- * width walked per lane (the five widest the instance allows; it fixes the
- * prefix width k = n - suffix bits, Section 3.1's split) and then the number
- * of resident 128-thread CTAs per SM of the walk kernel, and keeps the best
- * pair.  The choices
+ * integer dtypes; c and 2c instances, c = 2^36 / 2^n, at least 8 and at
+ * most 2048) and scores each configuration by the difference of their
+ * qbf_solve_batched times: the steady-state cost of c instances, as in a large
+ * mixed batch, without the last partial wave of one small launch.  It searches
+ * the suffix width walked per lane (the five widest the instance allows; it
+ * fixes the prefix width k = n - suffix bits, Section 3.1's split) and then
+ * the number of resident 128-thread CTAs per SM of the walk kernel.  It keeps
+ * the default pair (18 suffix bits or the widest allowed, the most CTAs per
+ * SM) unless another is faster by more than 2%, the run-to-run spread of the
+ * scores.  The choices
  * take effect at once in this process for the current device, and one line
  * per n is appended to `cache_path`:
  *     qbf-tune-v1 <device name> <SM count> <class> <n> <suffix bits> <CTAs/SM> <seconds>
@@ -380,7 +382,7 @@ int qbf_tune(int n_min, int n_max, int dtype, const char *cache_path);
 /* The batched solver's current choices for instances of n variables and
  * `dtype` on the current device (after qbf_tune or a loaded cache): suffix
  * bits walked per lane and CTAs per SM, 0 where nothing is tuned (then the
- * defaults apply: 16 suffix bits, as many CTAs as fit). */
+ * defaults apply: 18 suffix bits, as many CTAs as fit). */
 int qbf_tuned_params(int n, int dtype, int *suffix_bits, int *ctas_per_sm);
 
 /*

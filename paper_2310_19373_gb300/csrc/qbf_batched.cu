@@ -49,6 +49,8 @@ constexpr int kBatchThreads = 128;
 constexpr int kBatchWarps = kBatchThreads / 32;
 constexpr int kBatchR = kRMax;
 constexpr int kBatchMaxNS = 18;
+constexpr int kBatchDefaultNS = 18;  // suffix bits per lane when nothing is tuned
+constexpr double kTuneMargin = 0.02; // a tuned choice must beat the default by 2%
 constexpr int kBatchMinN = 11;  // smallest walk dimension: ns >= R and 32 prefixes per item
 // per warp: the 16-byte correction records of the two-pipe walk (128 x int4,
 // first so they stay 16-byte aligned) or the correction sums of the deferred
@@ -77,6 +79,8 @@ struct BatchArgs {
     const int *K;
     unsigned long long total_items;
     int *item_min;
+    unsigned *item_mask;  // per item: lanes whose minimum is within the window
+                          // of the item's minimum (the only ones EMIT walks)
     int *gmin;
     const unsigned *flagged;
     Counters *ctr;
@@ -126,6 +130,7 @@ __global__ void __launch_bounds__(kBatchThreads, (MODE == kModeMin && MIXK == 2)
     int *sS = sm[w] + 512;
     int *sLin = sS, *sK = sS, *sC = sS;
     int cur = -1, n = 0, ns = 0, tau = 0, ok = 0, exact = 0, use_mix = 0;
+    long long win = 0;
     unsigned long long nprefix = 0, item_off = 0;
     const int4 *rec4 = nullptr;
     const float *ftab_i = nullptr;
@@ -187,6 +192,7 @@ __global__ void __launch_bounds__(kBatchThreads, (MODE == kModeMin && MIXK == 2)
             // the lane needs R walked bits below its three group bits
             use_mix = (MODE == kModeMin) && MIXK && ok && ns >= kBatchR + 3 &&
                       plan->vhat <= (long long)kF32Vmax && (MIXK != 2 || ftab_i);
+            win = plan->window;
             if (MODE == kModeEmit && ok) {
                 const long long t = (long long)a.gmin[inst] + plan->window;
                 tau = (int)(t > (long long)INT_MAX ? (long long)INT_MAX : t);
@@ -223,38 +229,56 @@ __global__ void __launch_bounds__(kBatchThreads, (MODE == kModeMin && MIXK == 2)
 #pragma unroll
             for (int o = 16; o > 0; o >>= 1)
                 wm = min(wm, __shfl_xor_sync(0xffffffffu, wm, o));
+            // tau = gmin + W <= wm + W: only lanes within the window of the
+            // item's own minimum can hold a state <= tau
+            const unsigned mask =
+                __ballot_sync(0xffffffffu, active && (long long)m <= (long long)wm + win);
             if (lane == 0) {
                 a.item_min[gi] = wm;
+                a.item_mask[gi] = mask;
                 atomicMin(&a.gmin[inst], wm);
             }
-        } else if (exact) {
-            // W = 0: the values are exact, so only the lowest tied index of
-            // each lane can win; emit that one state per lane
-            unsigned GL[kBatchR];
-            const unsigned v = lane_setup<kBatchR>(p, n, ns, sS, sLin, sC, 32, lane, GL);
-            const unsigned long long pbase = p << ns;
-            unsigned long long best = ~0ull;
-            walk_suffix_visit<kBatchR>(v, GL, ns, rec4, sC, 32, lane, SmemK{sK},
-                                       [&](unsigned val, unsigned t) {
-                                           if ((int)val <= tau) {
-                                               const unsigned long long x =
-                                                   pbase | (unsigned long long)(t ^ (t >> 1));
-                                               best = x < best ? x : best;
-                                           }
-                                       });
-            if (active && best != ~0ull)
-                emit_candidate(a, best, inst);
         } else {
-            unsigned GL[kBatchR];
-            const unsigned v = lane_setup<kBatchR>(p, n, ns, sS, sLin, sC, 32, lane, GL);
-            const unsigned long long pbase = p << ns;
-            walk_suffix_visit<kBatchR>(v, GL, ns, rec4, sC, 32, lane, SmemK{sK},
-                                       [&](unsigned val, unsigned t) {
-                                           if ((int)val <= tau && active)
-                                               emit_candidate(
-                                                   a, pbase | (unsigned long long)(t ^ (t >> 1)),
-                                                   inst);
-                                       });
+            // EMIT: re-walk only the item's lanes in its mask, each prefix's
+            // 2^ns suffix states split into 2^j sub-walks of ns - j bits (its
+            // top j suffix variables fixed per lane), one per lane of the
+            // warp: the same states, 2^j times shorter per lane.  The block
+            // records of the ns-bit walk serve the shorter one (its first
+            // blocks flip the same variables), and the lane set-up takes the
+            // j fixed variables as prefix variables.
+            const unsigned mask = a.item_mask[gi];
+            const int j = min(5, ns - kBatchR);
+            const int nse = ns - j;
+            const bool sub_on = lane < (1 << j);
+            unsigned long long best = ~0ull;
+            for (unsigned mm = mask; mm; mm &= mm - 1) {
+                const unsigned long long pl = (gi - item_off) * 32 + (unsigned)(__ffs(mm) - 1);
+                const unsigned long long ps =
+                    (pl << j) | (unsigned long long)(sub_on ? lane : 0);
+                unsigned GL[kBatchR];
+                const unsigned v = lane_setup<kBatchR>(ps, n, nse, sS, sLin, sC, 32, lane, GL);
+                const unsigned long long pbase = ps << nse;
+                walk_suffix_visit<kBatchR>(
+                    v, GL, nse, rec4, sC, 32, lane, SmemK{sK}, [&](unsigned val, unsigned t) {
+                        if ((int)val <= tau && sub_on) {
+                            const unsigned long long x =
+                                pbase | (unsigned long long)(t ^ (t >> 1));
+                            if (exact)
+                                best = x < best ? x : best;  // W = 0: the lowest tie wins
+                            else
+                                emit_candidate(a, x, inst);
+                        }
+                    });
+            }
+            if (exact) {
+#pragma unroll
+                for (int o = 16; o > 0; o >>= 1) {
+                    const unsigned long long y = __shfl_xor_sync(0xffffffffu, best, o);
+                    best = y < best ? y : best;
+                }
+                if (lane == 0 && best != ~0ull)
+                    emit_candidate(a, best, inst);
+            }
         }
     }
 }
@@ -449,7 +473,7 @@ __global__ void batched_argmin_kernel(const unsigned long long *cand_idx,
 // host side
 
 struct BLayout {
-    size_t desc, plans, K, recs, item_min, flagged, gmin, best_key, best_idx, status, lowest,
+    size_t desc, plans, K, recs, item_min, item_mask, flagged, gmin, best_key, best_idx, status, lowest,
         ctr, cand_idx, cand_inst, keys, info, ftab, total;
 };
 
@@ -470,6 +494,7 @@ BLayout blayout(int count, unsigned long long nrec, unsigned long long items,
     L.K = take(sizeof(int) * 128 * count);
     L.recs = take(sizeof(Rec) * nrec);
     L.item_min = take(sizeof(int) * items);
+    L.item_mask = take(sizeof(unsigned) * items);
     L.flagged = take(sizeof(unsigned) * items);
     L.gmin = take(sizeof(int) * count);
     L.best_key = take(sizeof(unsigned long long) * count);
@@ -658,6 +683,7 @@ int enqueue_batch(BatchState &B, const BLayout &L, const BStage &S, int count,
     a.K = K;
     a.total_items = items;
     a.item_min = (int *)(d + L.item_min);
+    a.item_mask = (unsigned *)(d + L.item_mask);
     a.gmin = gmin;
     a.flagged = (const unsigned *)(d + L.flagged);
     a.ctr = ctr;
@@ -744,7 +770,7 @@ int solve_batched_mode(const void *const *Q, const int *n, const int *dtype, int
     if (o.batch_suffix_bits != 0 &&
         (o.batch_suffix_bits < kBatchR || o.batch_suffix_bits > kBatchMaxNS))
         return record_error(QBF_EINVAL, "batch_suffix_bits must be in [6, 18]");
-    const int NS_default = B.tuned_ns > 0 ? B.tuned_ns : 16;
+    const int NS_default = B.tuned_ns > 0 ? B.tuned_ns : kBatchDefaultNS;
     // states per (class, n): the n holding the most states picks the CTAs per SM
     double states_cn[2][QBF_BATCH_MAX_N + 1] = {};
 
@@ -1026,18 +1052,22 @@ __global__ void tune_fill_kernel(void *buf, int n, int dtype, unsigned long long
 
 // One n of qbf_tune.  A configuration is scored by the time difference between
 // a synthetic batch of 2c instances and one of c instances (c = 2^36 / 2^n,
-// at most 2048): the difference is the steady-state cost of c instances, free
-// of the last partial wave of work items, which in a single small launch
-// favours short walks but vanishes in a large mixed batch.  The suffix widths
+// at least 8 and at most 2048): the difference is the steady-state cost of c
+// instances, free of the last partial wave of work items, which in a single
+// small launch favours short walks but vanishes in a large mixed batch.  The
+// default configuration (kBatchDefaultNS suffix bits, the most CTAs per SM) is
+// scored first and kept unless another beats it by kTuneMargin: differences
+// below that are within the run-to-run spread of the scores, and a choice
+// made on noise alone measured slower in mixed batches.  The suffix widths
 // searched are the five widest the instance allows (narrower ones only add
-// per-prefix set-up), at the largest CTA count; then every CTA count at the
+// per-prefix set-up), at the most CTAs per SM; then every CTA count at the
 // best width.
 static int tune_one_n(int n, int dtype, cudaStream_t s, int *best_ns, int *best_ctas,
                       double *best_sec)
 {
     const int esz = dtsize(dtype);
     const unsigned long long c =
-        std::max<unsigned long long>(1, std::min<unsigned long long>(2048, (1ull << 36) >> n));
+        std::max<unsigned long long>(8, std::min<unsigned long long>(2048, (1ull << 36) >> n));
     const unsigned long long count = 2 * c;
     const unsigned long long per = (unsigned long long)n * n;
     void *buf = nullptr;
@@ -1096,12 +1126,16 @@ static int tune_one_n(int n, int dtype, cudaStream_t s, int *best_ns, int *best_
     const int nw = std::max(n, kBatchMinN);
     const int ns_hi = std::max(kBatchR, std::min(kBatchMaxNS, nw - 5));
     const int ns_lo = std::max(kBatchR, ns_hi - 4);
+    const int ns_def = std::max(kBatchR, std::min(kBatchDefaultNS, nw - 5));
     double bsec = 1e300;
-    int bns = ns_hi, bct = bps;
+    int bns = ns_def, bct = bps;
+    rc = score(ns_def, bps, &bsec);
     for (int ns = ns_lo; ns <= ns_hi && rc == QBF_OK; ++ns) {
+        if (ns == ns_def)
+            continue;
         double t = 0;
         rc = score(ns, bps, &t);
-        if (rc == QBF_OK && t < bsec) {
+        if (rc == QBF_OK && t < bsec * (1.0 - kTuneMargin)) {
             bsec = t;
             bns = ns;
         }
@@ -1109,7 +1143,7 @@ static int tune_one_n(int n, int dtype, cudaStream_t s, int *best_ns, int *best_
     for (int cc = 1; cc < bps && rc == QBF_OK; ++cc) {
         double t = 0;
         rc = score(bns, cc, &t);
-        if (rc == QBF_OK && t < bsec) {
+        if (rc == QBF_OK && t < bsec * (1.0 - kTuneMargin)) {
             bsec = t;
             bct = cc;
         }

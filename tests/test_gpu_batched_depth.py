@@ -40,7 +40,10 @@ def test_every_item_of_the_n34_instances_equals_oracle(batch, variant, walk):
     Qs, dev, picks = batch
     for inst in picks:
         n = Qs[inst].shape[0]
-        mins, nit, info = qb.batched_item_minima(dev, inst, 1 << 16, variant=variant)
+        # the default width, explicitly: a tuner run earlier in the process
+        # may have changed the process-wide default
+        mins, nit, info = qb.batched_item_minima(dev, inst, 1 << 16, batch_suffix_bits=16,
+                                                 variant=variant)
         inf = info[inst]
         assert inf.walk == walk
         s = inf.suffix_bits
