@@ -24,6 +24,20 @@ namespace qbf {
 constexpr int kMaxN = QBF_MAX_N;
 constexpr int kRMax = 6;  // low bits whose walk is unrolled at compile time
 
+// Two-limb images of the log Z walks (qbf_prepare.cu): each limb's sum of
+// |entries| is at most kLzLimbMax = 2^22, so the walks run exactly in FP32;
+// the lo limb carries logz_lo_bits(n) more bits: its entries are at most
+// 2^(L-1) in magnitude over n(n+1)/2 of them, L = 23 - ceil(log2(n(n+1)/2)),
+// at most 16.
+constexpr long long kLzLimbMax = 1ll << 22;
+__host__ __device__ constexpr int logz_lo_bits(int n)
+{
+    int c = 0;
+    while ((1ll << c) < (long long)n * (n + 1) / 2)
+        ++c;
+    return 23 - c < 16 ? 23 - c : 16;
+}
+
 // Written by the prepare kernel, read by every later kernel of a solve.
 struct Plan {
     int n;

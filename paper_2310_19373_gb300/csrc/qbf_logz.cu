@@ -6,13 +6,17 @@
 //   d min f / d Q_ij = x*_i x*_j                     (Danskin, x* = lowest argmin)
 //
 // Energies.  Each instance is walked on a two-limb fixed-point image
-// (qbf_prepare.cu: hi = round(y 2^s), lo = 16 more bits of the residual), i.e.
-// f at scale 2^(s+16) = hi_value * 2^16 + lo_value, both limbs walked exactly in
-// int32 in lockstep.  The shift m is the image value of the certified argmin
-// (from the batched minimiser), so every weight w = exp(-beta (f - m)) is <= ~1.
-// w = ex2(c (d_hi + d_lo 2^-16)) with d the limb differences to m and
-// c = -beta log2(e) 2^-s (the FP32 argument keeps 24 bits either way: the lo
-// limb matters only where d_hi is small).  Weights are summed in FP32 per block of
+// (qbf_prepare.cu: hi = round(y 2^s), lo = L more bits of the residual, L =
+// logz_lo_bits(n), 14 at n = 28), i.e. f at scale 2^(s+L) = hi_value * 2^L +
+// lo_value.  Each limb's sum of |entries| is at most 2^22, so both limbs walk
+// exactly in FP32, in lockstep as one packed pair: one packed add per field
+// and per correction, and no integer-to-float conversion per state (those
+// share the exponential unit with ex2, which bounds this walk).  The shift m
+// is the image value of the certified argmin (from the batched minimiser), so
+// every weight w = exp(-beta (f - m)) is <= ~1.  w = ex2(c (d_hi + d_lo 2^-L))
+// with d the limb differences to m and c = -beta log2(e) 2^-s (the FP32
+// argument keeps 24 bits either way: the lo limb matters only where d_hi is
+// small).  Weights are summed in FP32 per block of
 // 2^R states, blocks are added with Kahan compensation per lane, lanes in FP64
 // in a fixed order.
 //
@@ -37,6 +41,7 @@
 
 #include "qbf.h"
 #include "qbf_internal.cuh"
+#include "qbf_f32x2.cuh"
 #include "qbf_kernels.cuh"
 #include "qbf_walk_core.cuh"
 
@@ -58,6 +63,7 @@ struct LzArgs {
     const int *K;
     const int *shift;           // per instance and walk: (hi, lo) value of the argmin
     const float2 *cc;           // [b][kLzMaxBeta]: (c_hi, c_lo) of each beta
+    float lo_scale;             // 2^-L: weight of the lo limb
     int beta0;                  // first beta of this launch
     double *laneZ;              // MODE Z:  [b][lane][beta]
     double *laneM1;             // MODE M1: [b][lane][ns]
@@ -92,16 +98,19 @@ __device__ __forceinline__ void static_for(F &&f)
     }
 }
 
-// Two int32 walks (hi and lo limb) over the same suffix in lockstep.
-// visit(vh, vl, U, pi) is called at every state, with U the compile-time step
-// in the block (0 for the block's first state) and pi the block parity; the
-// low R bits of the state's Gray code are then gray(U), except bit R - 1,
-// which is gray(U)'s bit R - 1 xor pi.  flush(B) follows every block B.
+// Two FP32-exact walks (hi and lo limb) over the same suffix in lockstep, as
+// one packed pair v = (hi, lo).  The block records and the in-block
+// corrections hold FP32 bits (logz_tables_kernel), the lane parts of the mid
+// fields sCh / sCl are FP32.  visit(v, U, pi) is called at every state, with
+// U the compile-time step in the block (0 for the block's first state) and pi
+// the block parity; the low R bits of the state's Gray code are then gray(U),
+// except bit R - 1, which is gray(U)'s bit R - 1 xor pi.  flush(B) follows
+// every block B.
 template <int R, class F, class G>
-__device__ __forceinline__ void walk2(unsigned vh, unsigned (&GLh)[R], unsigned vl,
-                                      unsigned (&GLl)[R], int ns, const int4 *rh, const int4 *rl,
-                                      const int *sCh, const int *sCl, int stride, int slot,
-                                      const int2 *K2, F &&visit, G &&flush)
+__device__ __forceinline__ void walk2(f32x2::u64 v, f32x2::u64 (&GL)[R], int ns, const int4 *rh,
+                                      const int4 *rl, const float *sCh, const float *sCl,
+                                      int stride, int slot, const f32x2::u64 *K2, F &&visit,
+                                      G &&flush)
 {
     const int M = ns - R;
     const unsigned nblocks = 1u << M;
@@ -110,26 +119,29 @@ __device__ __forceinline__ void walk2(unsigned vh, unsigned (&GLh)[R], unsigned 
         if (B > 0) {
             const int4 ah = __ldg(rh + 2 * B), bh = __ldg(rh + 2 * B + 1);
             const int4 al = __ldg(rl + 2 * B), bl = __ldg(rl + 2 * B + 1);
-            vh = vh + (unsigned)ah.x + (unsigned)sCh[ah.y * stride + slot];
-            vl = vl + (unsigned)al.x + (unsigned)sCl[al.y * stride + slot];
+            const f32x2::u64 t = f32x2::pack(__int_as_float(ah.x), __int_as_float(al.x));
+            const f32x2::u64 c =
+                f32x2::pack(sCh[ah.y * stride + slot], sCl[al.y * stride + slot]);
+            v = f32x2::add(v, f32x2::add(t, c));
             const int Wh[6] = {ah.z, ah.w, bh.x, bh.y, bh.z, bh.w};
             const int Wl[6] = {al.z, al.w, bl.x, bl.y, bl.z, bl.w};
 #pragma unroll
-            for (int i = 0; i < R; ++i) {
-                GLh[i] += (unsigned)Wh[i];
-                GLl[i] += (unsigned)Wl[i];
-            }
+            for (int i = 0; i < R; ++i)
+                GL[i] = f32x2::add(GL[i],
+                                   f32x2::pack(__int_as_float(Wh[i]), __int_as_float(Wl[i])));
         }
-        visit(vh, vl, std::integral_constant<int, 0>{}, pi);
+        visit(v, std::integral_constant<int, 0>{}, pi);
         static_for<1, (1 << R)>([&](auto U) {
             constexpr int u = decltype(U)::value;
             constexpr int l = ctz_c(u);
             constexpr int g = u ^ (u >> 1);
             const int nb = ((g >> l) & 1) ^ ((l == R - 1) ? pi : 0);
-            const int2 k = K2[pi * 64 + u];  // both limbs' corrections, one load
-            vh = vh + (nb ? GLh[l] : 0u - GLh[l]) + (unsigned)k.x;
-            vl = vl + (nb ? GLl[l] : 0u - GLl[l]) + (unsigned)k.y;
-            visit(vh, vl, U, pi);
+            // the step's field and correction are added to each other off the
+            // chain of states, so the state chain is one packed add (every
+            // sum is an integer below 2^24 in magnitude: exact)
+            const f32x2::u64 k = K2[pi * 64 + u];  // both limbs' corrections, one load
+            v = f32x2::add(v, nb ? f32x2::add(k, GL[l]) : f32x2::sub(k, GL[l]));
+            visit(v, U, pi);
         });
         flush(B);
     }
@@ -178,6 +190,22 @@ __global__ void __launch_bounds__(kLzThreads) logz_walk_kernel(LzArgs a)
         lane_setup<R>(pp, n, ns, sSl, sLl, sCl, kLzThreads, threadIdx.x, GLl) - ml;
     const int4 *rh = reinterpret_cast<const int4 *>(a.recs + (size_t)pidx * a.rec_stride);
     const int4 *rl = reinterpret_cast<const int4 *>(a.recs + (size_t)(pidx + 1) * a.rec_stride);
+    // to FP32 (exact: every limb value is below 2^23 in magnitude): the start
+    // pair, the low-bit fields and this lane's parts of the mid-bit fields
+    const f32x2::u64 v0 = f32x2::pack((float)(int)vh, (float)(int)vl);
+    f32x2::u64 GL[R];
+#pragma unroll
+    for (int i = 0; i < R; ++i)
+        GL[i] = f32x2::pack((float)(int)GLh[i], (float)(int)GLl[i]);
+    for (int e = 0; e < 2 * (ns - R); ++e) {
+        int *ch = sCh + e * kLzThreads + threadIdx.x, *cl = sCl + e * kLzThreads + threadIdx.x;
+        *ch = __float_as_int((float)*ch);
+        *cl = __float_as_int((float)*cl);
+    }
+    const float *sChf = reinterpret_cast<const float *>(sCh);
+    const float *sClf = reinterpret_cast<const float *>(sCl);
+    const f32x2::u64 *sKf = reinterpret_cast<const f32x2::u64 *>(sK2);
+    const float lsc = a.lo_scale;
 
     if constexpr (MODE == kModeZ) {
         // NB betas (exactly a.nbeta for NB <= 4; up to NB = 8 with the rest
@@ -190,11 +218,13 @@ __global__ void __launch_bounds__(kLzThreads) logz_walk_kernel(LzArgs a)
             const float2 c2 = a.cc[(size_t)b * kLzMaxBeta + a.beta0 + j];
             ch[j] = c2.x;
         }
-        walk2<R>(vh, GLh, vl, GLl, ns, rh, rl, sCh, sCl, kLzThreads, threadIdx.x, sK2,
-                 [&](unsigned xh, unsigned xl, auto, int) {
-                     // c_lo = c_hi 2^-16 exactly, so c_hi dh + c_lo dl =
-                     // c_hi (dh + dl 2^-16): one FFMA per state, one FMUL per beta
-                     const float d = fmaf((float)(int)xl, 0x1p-16f, (float)(int)xh);
+        walk2<R>(v0, GL, ns, rh, rl, sChf, sClf, kLzThreads, threadIdx.x, sKf,
+                 [&](f32x2::u64 v, auto, int) {
+                     // c_lo = c_hi 2^-L exactly, so c_hi dh + c_lo dl =
+                     // c_hi (dh + dl 2^-L): one FFMA per state, one FMUL per beta
+                     float xh, xl;
+                     f32x2::unpack(v, xh, xl);
+                     const float d = fmaf(xl, lsc, xh);
 #pragma unroll
                      for (int j = 0; j < NB; ++j)
                          if (exact_nb || j < a.nbeta)
@@ -242,11 +272,13 @@ __global__ void __launch_bounds__(kLzThreads) logz_walk_kernel(LzArgs a)
         }
         for (int e = 0; e < 2 * NB * nmid; ++e)
             sMid[e * kLzThreads + threadIdx.x] = 0.f;
-        walk2<R>(vh, GLh, vl, GLl, ns, rh, rl, sCh, sCl, kLzThreads, threadIdx.x, sK2,
-                 [&](unsigned xh, unsigned xl, auto U, int pi) {
+        walk2<R>(v0, GL, ns, rh, rl, sChf, sClf, kLzThreads, threadIdx.x, sKf,
+                 [&](f32x2::u64 v, auto U, int pi) {
                      constexpr int u = decltype(U)::value;
                      constexpr int g = u ^ (u >> 1);
-                     const float d = fmaf((float)(int)xl, 0x1p-16f, (float)(int)xh);
+                     float xh, xl;
+                     f32x2::unpack(v, xh, xl);
+                     const float d = fmaf(xl, lsc, xh);
 #pragma unroll
                      for (int bb = 0; bb < NB; ++bb) {
                          const float w = ex2_approx(d * ch[bb]);
@@ -327,7 +359,7 @@ __global__ void __launch_bounds__(kLzThreads) logz_walk_kernel(LzArgs a)
 }
 
 // Per instance b and beta j < nbeta: c = -beta log2(e) 2^-sigma_b for the hi
-// limb and c 2^-16 for the lo limb, rounded from FP64 (entries j >= nbeta are
+// limb and c 2^-L for the lo limb, rounded from FP64 (entries j >= nbeta are
 // zero); st[b] = the instance's prepare status.
 __global__ void logz_consts_kernel(const Plan *plans, const double *beta, int nbeta, int batch,
                                    float2 *cc, int *st)
@@ -341,7 +373,7 @@ __global__ void logz_consts_kernel(const Plan *plans, const double *beta, int nb
         float2 v = make_float2(0.f, 0.f);
         if (j < nbeta) {
             const double c = -beta[j] * 1.4426950408889634 * ldexp(1.0, -P->sigma);
-            v = make_float2((float)c, (float)(c * ldexp(1.0, -16)));
+            v = make_float2((float)c, (float)(c * ldexp(1.0, P->sigma - P[1].sigma)));
         }
         cc[(size_t)b * kLzMaxBeta + j] = v;
     }
@@ -410,8 +442,9 @@ __global__ void __launch_bounds__(256) logz_reduce_kernel(const Plan *plans, con
                 logz[b * nbeta + j] = NAN;
                 continue;
             }
-            const long long m = ((long long)shift[b * 4] << 16) + (long long)shift[b * 4 + 1];
-            const double mreal = ldexp((double)m, -(ph->sigma + 16));
+            const int L = ph[1].sigma - ph->sigma;
+            const long long m = ((long long)shift[b * 4] << L) + (long long)shift[b * 4 + 1];
+            const double mreal = ldexp((double)m, -ph[1].sigma);
             logz[b * nbeta + j] = -beta[j] * mreal + log(Z);
         }
     }
@@ -728,6 +761,7 @@ LzArgs lz_args(const LzGeo &g, char *base, const LzLayout &L, int walk, int nbet
     a.laneZ = (double *)(base + (walk ? L.laneZB : L.laneZA));
     a.laneM1 = (double *)(base + L.laneM1);
     a.cc = (const float2 *)(base + L.cc);
+    a.lo_scale = (float)ldexp(1.0, -logz_lo_bits(g.n));
     a.beta0 = 0;
     (void)beta;
     return a;

@@ -300,11 +300,14 @@ __global__ void __launch_bounds__(256) batched_tables_kernel(const BatchDesc *de
 //
 // For instance b and walk w (0: identity order, 1: variables rotated so that
 // walk variable v is the caller's variable (v + rot) mod n), writes two Plans:
-// hi = round(y * 2^sigma) and lo = round((y * 2^sigma - hi) * 2^16) for every
-// lin / S entry y.  Both limbs are exact int32 images (|lo| <= 2^15), so
-// hi * 2^16 + lo is the fixed-point value at scale 2^(sigma + 16), walked
-// exactly as two int32 walks in lockstep.  sigma comes from the unrotated
-// order so both walks share it.
+// hi = round(y * 2^sigma) and lo = round((y * 2^sigma - hi) * 2^L) for every
+// lin / S entry y, L = logz_lo_bits(n).  sigma keeps sum |hi| <= 2^22, and
+// |lo| <= 2^(L-1) over at most n(n+1)/2 entries keeps sum |lo| <= 2^22, so
+// every value the walk forms (a state's value minus the shift, plus one field
+// or correction) stays below 3 * 2^22 < 2^24 in each limb: both limbs walk
+// exactly in FP32, as one packed pair.  hi * 2^L + lo is the fixed-point value
+// at scale 2^(sigma + L).  sigma comes from the unrotated order so both walks
+// share it.
 __global__ void __launch_bounds__(256) logz_prepare_kernel(const void *Q, int n, int dtype,
                                                            int rot, Plan *plans)
 {
@@ -342,9 +345,10 @@ __global__ void __launch_bounds__(256) logz_prepare_kernel(const void *Q, int n,
         return;
     }
     const double V_sym = block_sum_d(vs, redd);
+    const double limb_max = (double)kLzLimbMax;
     int sigma = 0;
     if (V_sym > 0.0) {
-        sigma = ilogb((2147483647.0 - (double)nn) / V_sym);
+        sigma = ilogb((limb_max - (double)nn) / V_sym);
         sigma = max(-1000, min(1000, sigma));
     }
     for (int iter = 0; iter < 64; ++iter) {
@@ -356,15 +360,16 @@ __global__ void __launch_bounds__(256) logz_prepare_kernel(const void *Q, int n,
             const double y = (i == j) ? sQ[e] : sQ[e] + sQ[j * n + i];
             part += llabs(__double2ll_rn(ldexp(y, sigma)));
         }
-        if (block_sum_ll(part, redl) <= (long long)INT_MAX)
+        if (block_sum_ll(part, redl) <= kLzLimbMax)
             break;
         --sigma;
     }
+    const int L = logz_lo_bits(n);
     for (int e = t; e < nn; e += blockDim.x) {
         const int i = e / n, j = e % n;
         const double y = (i == j) ? ldexp(sQ[e], sigma) : ldexp(sQ[e] + sQ[j * n + i], sigma);
         const long long h = __double2ll_rn(y);
-        const long long l = __double2ll_rn(ldexp(y - (double)h, 16));
+        const long long l = __double2ll_rn(ldexp(y - (double)h, L));
         if (i == j) {
             hi->lin[i] = (int)h;
             lo->lin[i] = (int)l;
@@ -378,7 +383,7 @@ __global__ void __launch_bounds__(256) logz_prepare_kernel(const void *Q, int n,
         hi->n = lo->n = n;
         hi->dtype = lo->dtype = dtype;
         hi->sigma = sigma;
-        lo->sigma = sigma + 16;
+        lo->sigma = sigma + L;
         hi->window = lo->window = 0;
         hi->status = lo->status = QBF_OK;
     }
@@ -396,8 +401,20 @@ __global__ void __launch_bounds__(256) logz_tables_kernel(const Plan *plans, int
     const int ns = w ? nsB : nsA;
     const int R = min(kRMax, ns);
     const unsigned nrec = 1u << (ns - R);
-    for (unsigned B = threadIdx.x; B < max(nrec, 128u); B += blockDim.x)
-        tables_body(plan, ns, R, recs + (size_t)pi * rec_stride, nrec, K + pi * 128, B);
+    Rec *rp = recs + (size_t)pi * rec_stride;
+    int *Kp = K + pi * 128;
+    for (unsigned B = threadIdx.x; B < max(nrec, 128u); B += blockDim.x) {
+        tables_body(plan, ns, R, rp, nrec, Kp, B);
+        // the log Z walks add these in FP32 (exact: |value| <= 2 * 2^22); this
+        // thread wrote exactly the entries of index B
+        if (B < 128)
+            Kp[B] = __float_as_int((float)Kp[B]);
+        if (B > 0 && B < nrec) {
+            rp[B].T = __float_as_int((float)rp[B].T);
+            for (int i = 0; i < kRMax; ++i)
+                rp[B].W[i] = __float_as_int((float)rp[B].W[i]);
+        }
+    }
 }
 
 }  // namespace qbf
