@@ -48,19 +48,28 @@ namespace {
 constexpr int kBatchThreads = 128;
 constexpr int kBatchWarps = kBatchThreads / 32;
 constexpr int kBatchR = kRMax;
+// the table-driven deferred walk's block: 2^7 = 128 steps (its seventh field
+// from the lane's shared memory, as in the single-solve kernel)
+constexpr int kBatchDeferR = 7;
 constexpr int kBatchMaxNS = 18;
 constexpr int kBatchDefaultNS = 18;  // suffix bits per lane when nothing is tuned
 constexpr double kTuneMargin = 0.02; // a tuned choice must beat the default by 2%
 constexpr int kBatchMinN = 11;  // smallest walk dimension: ns >= R and 32 prefixes per item
-// per warp: the 16-byte correction records of the two-pipe walk (128 x int4,
-// first so they stay 16-byte aligned) or the correction sums of the deferred
-// walk (128 floats), then S, lin, K and the lane parts of the fields
+// per warp: a 16-byte aligned head -- the correction records of the two-pipe
+// walk (128 x int4), or for the table-driven deferred walk the double buffer
+// of F values (2 x 128 floats), the group terms of the mid variables (at most
+// (kBatchMaxNS - 3 - kBatchDeferR) x 16 floats) and the lanes' seventh field
+// (32 lanes x 2 x 16 bytes) -- then S, lin, K and the lane parts of the fields
+constexpr int kWarpHeadInts = 640;
+static_assert(2 * (1 << kBatchDeferR) + (kBatchMaxNS - 3 - kBatchDeferR) * 16 + 32 * 8 <=
+                  kWarpHeadInts,
+              "deferred-walk head of the warp slice");
 constexpr int kWarpSmemInts =
-    (512 + QBF_BATCH_MAX_N * QBF_BATCH_MAX_N + QBF_BATCH_MAX_N + 128 +
+    (kWarpHeadInts + QBF_BATCH_MAX_N * QBF_BATCH_MAX_N + QBF_BATCH_MAX_N + 128 +
      2 * (kBatchMaxNS - kBatchR) * 32 + 3) & ~3;
 constexpr unsigned long long kBatchCandCap = 1ull << 20;
 // resident CTAs per SM asked of the table-driven deferred MIN kernel (bounded
-// by the 41.6 KB of shared memory per CTA: five fit in 228 KB)
+// by the 43.6 KB of shared memory per CTA: five fit in 228 KB)
 constexpr int kBatchDeferCtas = 5;
 
 // per-instance certification details, filled on the device (qbf_batch_info)
@@ -127,7 +136,7 @@ __global__ void __launch_bounds__(kBatchThreads, (MODE == kModeMin && MIXK == 2)
     __shared__ __align__(16) int sm[kBatchWarps][kWarpSmemInts];
     const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
     int4 *sKx = reinterpret_cast<int4 *>(sm[w]);
-    int *sS = sm[w] + 512;
+    int *sS = sm[w] + kWarpHeadInts;
     int *sLin = sS, *sK = sS, *sC = sS;
     int cur = -1, n = 0, ns = 0, tau = 0, ok = 0, exact = 0, use_mix = 0;
     long long win = 0;
@@ -172,14 +181,14 @@ __global__ void __launch_bounds__(kBatchThreads, (MODE == kModeMin && MIXK == 2)
                     sKx[e] = make_int4(kf, kf, k, 0);
             }
             if (MODE == kModeMin && MIXK == 2 && ftab_i) {
-                // the table-driven deferred walk: the first 128 words of the
-                // slice are the warp's double buffer of F values, then the
-                // group terms of every mid variable, both directions
+                // the table-driven deferred walk: the head of the slice holds
+                // the warp's double buffer of F values, then the group terms
+                // of every mid variable, both directions
                 __syncwarp();
                 const int nsw = ns - 3;
-                float4 *sE = reinterpret_cast<float4 *>(sm[w] + 128);
-                for (int e = lane; e < (nsw - kBatchR) * 2; e += 32) {
-                    const int i = kBatchR + (e >> 1);
+                float4 *sE = reinterpret_cast<float4 *>(sm[w] + 2 * (1 << kBatchDeferR));
+                for (int e = lane; e < (nsw - kBatchDeferR) * 2; e += 32) {
+                    const int i = kBatchDeferR + (e >> 1);
                     const float sg = (e & 1) ? 1.f : -1.f;
                     const float s0 = (float)sS[i * n + nsw], s1 = (float)sS[i * n + nsw + 1];
                     const float s2 = (float)sS[i * n + nsw + 2];
@@ -190,7 +199,8 @@ __global__ void __launch_bounds__(kBatchThreads, (MODE == kModeMin && MIXK == 2)
             }
             // eight-prefix walks: every partial sum must be exact in FP32, and
             // the lane needs R walked bits below its three group bits
-            use_mix = (MODE == kModeMin) && MIXK && ok && ns >= kBatchR + 3 &&
+            use_mix = (MODE == kModeMin) && MIXK && ok &&
+                      ns >= (MIXK == 2 ? kBatchDeferR : kBatchR) + 3 &&
                       plan->vhat <= (long long)kF32Vmax && (MIXK != 2 || ftab_i);
             win = plan->window;
             if (MODE == kModeEmit && ok) {
@@ -209,13 +219,16 @@ __global__ void __launch_bounds__(kBatchThreads, (MODE == kModeMin && MIXK == 2)
         if constexpr (MODE == kModeMin) {
             int m;
             if (MIXK == 2 && use_mix) {
-                dfr2::Lane<kBatchR> L;
+                constexpr int RD = kBatchDeferR;
+                constexpr int kE = 2 * (1 << RD);                     // group terms
+                constexpr int kG = kE + (kBatchMaxNS - 3 - RD) * 16;  // seventh fields
+                dfr2::Lane<RD> L;
                 float *sCf = reinterpret_cast<float *>(sC);
-                dfr2::setup<kBatchR>(L, p, n, ns, sS, sLin, sCf, 32, lane, nullptr);
-                m = dfr2::walk_min<kBatchR>(L, ns - 3, ftab_i, reinterpret_cast<float *>(sm[w]),
-                                            lane, sCf, 32, lane,
-                                            reinterpret_cast<const float4 *>(sm[w] + 128),
-                                            nullptr);
+                ulonglong2 *sGFx = reinterpret_cast<ulonglong2 *>(sm[w] + kG);
+                dfr2::setup<RD>(L, p, n, ns, sS, sLin, sCf, 32, lane, sGFx);
+                m = dfr2::walk_min<RD>(L, ns - 3, ftab_i, reinterpret_cast<float *>(sm[w]), lane,
+                                       sCf, 32, lane, reinterpret_cast<const float4 *>(sm[w] + kE),
+                                       sGFx);
             } else if (MIXK == 1 && use_mix) {
                 mix::Lane<kBatchR> L;
                 mix::setup<kBatchR>(L, p, n, ns, sS, sLin, sC, 32, lane);
@@ -448,7 +461,8 @@ __global__ void batched_info_kernel(const BatchDesc *desc, int count, const Plan
     const bool is_int = (desc[i].dtype == QBF_I32 || desc[i].dtype == QBF_I16);
     info[i].sigma = plan->sigma;
     info[i].error_bound = is_int ? 0.0 : plan->error_bound;
-    const bool eight = mix && plan->status == QBF_OK && desc[i].ns >= kBatchR + 3 &&
+    const bool eight = mix && plan->status == QBF_OK &&
+                       desc[i].ns >= (mix == 2 ? kBatchDeferR : kBatchR) + 3 &&
                        plan->vhat <= (long long)kF32Vmax;
     info[i].walk = eight ? (mix == 2 ? QBF_VARIANT_SPLIT_DEFER : QBF_VARIANT_SPLIT_MIX)
                          : QBF_VARIANT_SPLIT;
@@ -803,7 +817,7 @@ int solve_batched_mode(const void *const *Q, const int *n, const int *dtype, int
         d.ftab_off = ~0ull;
         items += (d.nprefix + 31) / 32;
         nrec += 1ull << (d.ns - kBatchR);
-        if (mix == 2 && d.ns >= kBatchR + 3) {
+        if (mix == 2 && d.ns >= kBatchDeferR + 3) {
             // suffix table of the table-driven deferred walk: 2^(ns - 3) floats,
             // a multiple of 64, so every block of it starts 256-byte aligned
             d.ftab_off = nftab;
