@@ -408,9 +408,12 @@ int qbf_tune_batched(const void *const *Q_dev, const int *n, const int *dtype, i
  * logz    : host, batch * nbeta (logz[b * nbeta + j]).
  * min_value, argmin : host, batch entries; the certified minimum and lowest
  *           argmin (as qbf_solve_batched), which also fix the shift m.
- * Energies come from an exact two-limb fixed-point image of Q (resolution
- * 2^-(sigma+16) of f); weights exp(-beta (f - m)) are FP32, summed in FP32 per
- * block, Kahan-compensated per thread and in FP64 across threads.
+ * Energies come from an exact two-limb fixed-point image of Q.  Each limb's
+ * entries sum to at most 2^22 in magnitude, so both limbs walk exactly in
+ * FP32.  The resolution is 2^-(sigma+L) of f, where sigma is the hi limb's
+ * scale and L = 23 - ceil(log2(n(n+1)/2)), at most 16 (14 at n = 28).  The
+ * weights exp(-beta (f - m)) are FP32, summed in FP32 per block,
+ * Kahan-compensated per thread, and summed in FP64 across threads.
  */
 int qbf_logz(const void *Q_dev, int n, int dtype, int batch, const double *beta, int nbeta,
              double *logz, double *min_value, uint64_t *argmin, void *stream);
