@@ -426,17 +426,20 @@ __global__ void batched_rescore_kernel(const BatchDesc *desc, const unsigned lon
 
 // Suffix tables of the table-driven deferred walk: F(gray(t)) for t <
 // 2^(ns - 3) on the instance's image (int64 sums, exact in FP32 since the
-// image fits 2^23 whenever the walk uses them).  One CTA per instance.
+// image fits 2^23 whenever the walk uses them).  kFtabSplit CTAs per
+// instance, each taking every kFtabSplit-th run of blockDim.x entries.
+constexpr int kFtabSplit = 8;
 __global__ void batched_ftab_kernel(const BatchDesc *desc, const Plan *plans, float *ftab)
 {
-    const BatchDesc d = desc[blockIdx.x];
+    const int inst = blockIdx.x / kFtabSplit, part = blockIdx.x % kFtabSplit;
+    const BatchDesc d = desc[inst];
     if (d.ftab_off == ~0ull)
         return;
-    const Plan *plan = plans + blockIdx.x;
+    const Plan *plan = plans + inst;
     const int n = d.n;
     const unsigned N = 1u << (d.ns - 3);
     float *out = ftab + d.ftab_off;
-    for (unsigned t = threadIdx.x; t < N; t += blockDim.x) {
+    for (unsigned t = part * blockDim.x + threadIdx.x; t < N; t += kFtabSplit * blockDim.x) {
         const unsigned x = t ^ (t >> 1);
         long long f = 0;
         for (unsigned r = x; r; r &= r - 1) {
@@ -687,7 +690,7 @@ int enqueue_batch(BatchState &B, const BLayout &L, const BStage &S, int count,
                                                  mix ? kF32Vmax : (long long)INT_MAX);
     batched_tables_kernel<<<count, 256, 0, s>>>(desc, plans, recs, K);
     if (mix == 2)
-        batched_ftab_kernel<<<count, 256, 0, s>>>(desc, plans, (float *)(d + L.ftab));
+        batched_ftab_kernel<<<count * kFtabSplit, 256, 0, s>>>(desc, plans, (float *)(d + L.ftab));
     BatchArgs a;
     memset(&a, 0, sizeof(a));
     a.desc = desc;

@@ -450,91 +450,169 @@ __global__ void __launch_bounds__(256) logz_reduce_kernel(const Plan *plans, con
     }
 }
 
+// Sums of a per-lane value v(p) over the 2^k lanes of a walk, split by the
+// lane index p = r 2^l + c into rows r (the high h = k - l bits) and columns
+// c (the low l = k / 2 <= 8 bits): rows[r] = sum_c v, cols[c] = sum_r v and,
+// when y is given, y[r * 8 + t] = sum_c [bit t of c] v for t < l.  Each entry
+// is summed by one thread in ascending order, so the sums do not depend on
+// scheduling.  Every pair sum sum_p v(p) [p_s] [p_t] then follows from these
+// tables in O(2^h + 2^l) adds instead of O(2^k) per pair.
+template <class V>
+__device__ void lz_rows_cols(const V &v, int k, double *rows, double *cols, double *y)
+{
+    const int l = k / 2, h = k - l;
+    const unsigned C = 1u << l, Rn = 1u << h;
+    for (unsigned r = threadIdx.x; r < Rn; r += blockDim.x) {
+        double sr = 0.0, yy[8];
+#pragma unroll
+        for (int t = 0; t < 8; ++t)
+            yy[t] = 0.0;
+        for (unsigned c = 0; c < C; ++c) {
+            const double x = v((unsigned long long)r * C + c);
+            sr += x;
+            if (y) {
+#pragma unroll
+                for (int t = 0; t < 8; ++t)
+                    if (t < l && ((c >> t) & 1u))  // c is the same in every lane
+                        yy[t] += x;
+            }
+        }
+        rows[r] = sr;
+        if (y) {
+#pragma unroll
+            for (int t = 0; t < 8; ++t)
+                y[r * 8 + t] = yy[t];
+        }
+    }
+    for (unsigned c = threadIdx.x; c < C; c += blockDim.x) {
+        double sc = 0.0;
+        for (unsigned r = 0; r < Rn; ++r)
+            sc += v((unsigned long long)r * C + c);
+        cols[c] = sc;
+    }
+}
+
+// sum_p v(p) [p_s] [p_t] (s <= t < k) from the tables of lz_rows_cols
+__device__ double lz_pair_sum(int k, int s, int t, const double *rows, const double *cols,
+                              const double *y)
+{
+    const int l = k / 2, h = k - l;
+    double a = 0.0;
+    if (t < l) {
+        for (unsigned c = 0; c < (1u << l); ++c)
+            if (((c >> s) & 1u) && ((c >> t) & 1u))
+                a += cols[c];
+    } else if (s >= l) {
+        for (unsigned r = 0; r < (1u << h); ++r)
+            if (((r >> (s - l)) & 1u) && ((r >> (t - l)) & 1u))
+                a += rows[r];
+    } else {
+        for (unsigned r = 0; r < (1u << h); ++r)
+            if ((r >> (t - l)) & 1u)
+                a += y[r * 8 + s];
+    }
+    return a;
+}
+
+// sum_p v(p) [p_t] from the row and column sums
+__device__ double lz_bit_sum(int k, int t, const double *rows, const double *cols)
+{
+    const int l = k / 2, h = k - l;
+    double a = 0.0;
+    if (t < l) {
+        for (unsigned c = 0; c < (1u << l); ++c)
+            if ((c >> t) & 1u)
+                a += cols[c];
+    } else {
+        for (unsigned r = 0; r < (1u << h); ++r)
+            if ((r >> (t - l)) & 1u)
+                a += rows[r];
+    }
+    return a;
+}
+
 // E[x_i x_j] for one beta from walk A (Z, M1) and walk B (Z); adds
-// up[b] * (-beta) * E into grad and optionally stores E.  One block per
-// (instance b, row i): every thread accumulates its share of the lanes for
-// every j >= i in registers, then each column is reduced by a fixed tree, so
-// the sums do not depend on scheduling.
+// up[b] * (-beta) * E into grad and optionally stores E.  Grid (instance b,
+// part): part 0 takes the pairs of top variables (walk A's prefix bits, from
+// its per-lane Z), part 1 the pairs of bottom variables (walk B's prefix bits,
+// from its per-lane Z), part 2 + i the bottom variable i against every top
+// variable (walk A's first moments of bit i).  Dynamic shared memory:
+// lz_moments_smem(n) bytes.  Every sum has a fixed order.
 __global__ void __launch_bounds__(256) logz_moments_kernel(
     int n, int nsA, unsigned long long lanesA, unsigned long long lanesB, const double *ZA,
     const double *M1A, const double *ZB, int zb_stride, int zb_off, double beta,
     const double *up, int up_stride, int up_off, double *grad, double *moment,
     int moment_stride, int moment_off)
 {
-    __shared__ double red[256];
-    const int b = blockIdx.x / n, i = blockIdx.x % n;
+    extern __shared__ double lzm[];
+    const int b = blockIdx.x, part = blockIdx.y;
+    const int kA = n - nsA, kB = nsA;
     const double *za = ZA + (size_t)b * lanesA;
     const double *m1 = M1A + (size_t)b * lanesA * nsA;
     const double *zb = ZB + (size_t)b * lanesB * zb_stride + zb_off;  // beta column
-    double acc[QBF_BATCH_MAX_N];
-#pragma unroll
-    for (int j = 0; j < QBF_BATCH_MAX_N; ++j)
-        acc[j] = 0.0;
-    if (i >= nsA) {
-        // both top: prefix bits of walk A
-        const int bi = i - nsA;
-        for (unsigned long long p = threadIdx.x; p < lanesA; p += blockDim.x) {
-            if (!((p >> bi) & 1ull))
-                continue;
-            const double z = __ldg(za + p);
-#pragma unroll
-            for (int j = 0; j < QBF_BATCH_MAX_N; ++j)
-                if (j >= i && j < n && ((p >> (j - nsA)) & 1ull))
-                    acc[j] += z;
-        }
-    } else {
-        // i bottom, j bottom: prefix bits i, j of walk B
-        for (unsigned long long p = threadIdx.x; p < lanesB; p += blockDim.x) {
-            if (!((p >> i) & 1ull))
-                continue;
-            const double z = __ldg(zb + p * zb_stride);
-#pragma unroll
-            for (int j = 0; j < QBF_BATCH_MAX_N; ++j)
-                if (j >= i && j < nsA && ((p >> j) & 1ull))
-                    acc[j] += z;
-        }
-        // i bottom, j top: walk A's first moments of bit i
-        for (unsigned long long p = threadIdx.x; p < lanesA; p += blockDim.x) {
-            const double v = __ldg(m1 + p * nsA + i);
-#pragma unroll
-            for (int j = 0; j < QBF_BATCH_MAX_N; ++j)
-                if (j >= nsA && j < n && ((p >> (j - nsA)) & 1ull))
-                    acc[j] += v;
-        }
-    }
-    const double ZAt = block_sum_fixed(za, lanesA, 1, red);
-    const double ZBt = block_sum_fixed(zb, lanesB, zb_stride, red);
-    const double u = up ? up[b * up_stride + up_off] : 1.0;
-    // every column j at once: a fixed-order shuffle sum per warp, then the
-    // warps' partial sums in warp order (deterministic)
-    __shared__ double part[256 / 32][QBF_BATCH_MAX_N];
-    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-#pragma unroll
-    for (int j = 0; j < QBF_BATCH_MAX_N; ++j) {
-        double v = acc[j];
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1)
-            v += __shfl_down_sync(0xffffffffu, v, o);
-        if (lane == 0)
-            part[wid][j] = v;
+    const int k = (part == 1) ? kB : kA;
+    const int hk = k - k / 2;
+    double *rows = lzm, *cols = rows + (1u << hk), *y = cols + (1u << (k / 2));
+    double *tot = y + (1u << hk) * 8;
+    auto vA = [&](unsigned long long p) { return __ldg(za + p); };
+    auto vB = [&](unsigned long long p) { return __ldg(zb + p * zb_stride); };
+    if (part == 1)
+        lz_rows_cols(vB, k, rows, cols, y);
+    else
+        lz_rows_cols(vA, k, rows, cols, part == 0 ? y : nullptr);
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double t = 0.0;
+        for (unsigned r = 0; r < (1u << hk); ++r)
+            t += rows[r];
+        tot[0] = t;
     }
     __syncthreads();
-    const int j = threadIdx.x;
-    if (j >= i && j < n) {
-        double sum = 0.0;
-        for (int w = 0; w < (int)(blockDim.x >> 5); ++w)
-            sum += part[w][j];
-        const double E = sum / ((i < nsA && j < nsA) ? ZBt : ZAt);
+    const double Zt = tot[0];  // walk B's total for part 1, walk A's otherwise
+    const double u = up ? up[b * up_stride + up_off] : 1.0;
+    auto emit = [&](int vi, int vj, double sum) {
+        const double E = sum / Zt;
         const double gval = u * (-beta) * E;
-        grad[(size_t)b * n * n + i * n + j] += gval;
-        if (i != j)
-            grad[(size_t)b * n * n + j * n + i] += gval;
+        grad[(size_t)b * n * n + vi * n + vj] += gval;
+        if (vi != vj)
+            grad[(size_t)b * n * n + vj * n + vi] += gval;
         if (moment) {
             double *mm = moment + (size_t)b * moment_stride + moment_off;
-            mm[i * n + j] = E;
-            mm[j * n + i] = E;
+            mm[vi * n + vj] = E;
+            mm[vj * n + vi] = E;
         }
+    };
+    if (part <= 1) {
+        // walk A's prefix bit t is variable nsA + t, walk B's is variable t
+        const int off = (part == 0) ? nsA : 0;
+        const int npairs = k * (k + 1) / 2;
+        for (int q = threadIdx.x; q < npairs; q += blockDim.x) {
+            int s = 0, rem = q;
+            while (rem >= k - s) {
+                rem -= k - s;
+                ++s;
+            }
+            const int t = s + rem;
+            emit(off + s, off + t, lz_pair_sum(k, s, t, rows, cols, y));
+        }
+    } else {
+        const int i = part - 2;
+        auto vM = [&](unsigned long long p) { return __ldg(m1 + p * nsA + i); };
+        lz_rows_cols(vM, kA, rows, cols, nullptr);  // Z's tables are no longer read
+        __syncthreads();
+        for (int t = threadIdx.x; t < kA; t += blockDim.x)
+            emit(i, nsA + t, lz_bit_sum(kA, t, rows, cols));
     }
+}
+
+size_t lz_moments_smem(int n)
+{
+    int hmax = 0, lmax = 0;
+    for (int k : {n - n / 2, n / 2}) {
+        hmax = std::max(hmax, k - k / 2);
+        lmax = std::max(lmax, k / 2);
+    }
+    return sizeof(double) * (((size_t)1 << hmax) * 9 + ((size_t)1 << lmax) + 1);
 }
 
 __global__ void danskin_kernel(const unsigned long long *argmin, int n, int batch,
@@ -860,7 +938,7 @@ int logz_backward(const void *Q, int n, int dtype, int batch, const double *beta
         for (int jj = 0; jj < nb; ++jj) {
             const int j = j0 + jj;
             const size_t slab = (size_t)jj * batch * g.lanesA;
-            logz_moments_kernel<<<batch * n, 256, 0, s>>>(
+            logz_moments_kernel<<<dim3(batch, 2 + g.nsA), 256, lz_moments_smem(n), s>>>(
                 n, g.nsA, g.lanesA, g.lanesB, (const double *)(base + L.laneZA) + slab,
                 (const double *)(base + L.laneM1) + slab * g.nsA,
                 (const double *)(base + L.laneZB), nbeta, j, beta[j], upstream, nbeta, j, grad,
