@@ -143,8 +143,18 @@ __global__ void __launch_bounds__(kBatchThreads, (MODE == kModeMin && MIXK == 2)
     unsigned long long nprefix = 0, item_off = 0;
     const int4 *rec4 = nullptr;
     const float *ftab_i = nullptr;
+    // EMIT: each flagged item is 2^sx work units, so that a few flagged items
+    // still spread over the grid (at least four units per resident warp,
+    // while an item's prefixes split into at most 2^10 sub-walks)
+    int sx = 0;
+    if (MODE == kModeEmit) {
+        const unsigned long long fl = a.ctr->flagged;
+        const unsigned long long want = 4ull * gridDim.x * kBatchWarps;
+        while (sx < 5 && (fl << sx) < want)
+            ++sx;
+    }
     const unsigned long long total =
-        (MODE == kModeMin) ? a.total_items : (unsigned long long)a.ctr->flagged;
+        (MODE == kModeMin) ? a.total_items : ((unsigned long long)a.ctr->flagged << sx);
 
     while (true) {
         unsigned long long g = 0;
@@ -153,7 +163,8 @@ __global__ void __launch_bounds__(kBatchThreads, (MODE == kModeMin && MIXK == 2)
         g = __shfl_sync(0xffffffffu, g, 0);
         if (g >= total)
             break;
-        const unsigned long long gi = (MODE == kModeMin) ? g : (unsigned long long)a.flagged[g];
+        const unsigned long long gi =
+            (MODE == kModeMin) ? g : (unsigned long long)a.flagged[g >> sx];
         const int inst = find_instance(a.desc, a.count, gi);
         if (inst != cur) {
             __syncwarp();
@@ -254,20 +265,23 @@ __global__ void __launch_bounds__(kBatchThreads, (MODE == kModeMin && MIXK == 2)
         } else {
             // EMIT: re-walk only the item's lanes in its mask, each prefix's
             // 2^ns suffix states split into 2^j sub-walks of ns - j bits (its
-            // top j suffix variables fixed per lane), one per lane of the
-            // warp: the same states, 2^j times shorter per lane.  The block
+            // top j suffix variables fixed per sub-walk): the same states,
+            // 2^j times shorter per lane.  Unit g takes sub-walks 32 (g mod
+            // 2^sx) .. + 31 of every masked prefix, one per lane.  The block
             // records of the ns-bit walk serve the shorter one (its first
             // blocks flip the same variables), and the lane set-up takes the
             // j fixed variables as prefix variables.
             const unsigned mask = a.item_mask[gi];
-            const int j = min(5, ns - kBatchR);
+            const int j = min(5 + sx, ns - kBatchR);
             const int nse = ns - j;
-            const bool sub_on = lane < (1 << j);
+            const unsigned sub = ((unsigned)(g & ((1ull << sx) - 1)) << 5) + (unsigned)lane;
+            const bool sub_on = sub < (1u << j);
+            if (!__any_sync(0xffffffffu, sub_on))
+                continue;  // a short walk has fewer sub-walks than units
             unsigned long long best = ~0ull;
             for (unsigned mm = mask; mm; mm &= mm - 1) {
                 const unsigned long long pl = (gi - item_off) * 32 + (unsigned)(__ffs(mm) - 1);
-                const unsigned long long ps =
-                    (pl << j) | (unsigned long long)(sub_on ? lane : 0);
+                const unsigned long long ps = (pl << j) | (unsigned long long)(sub_on ? sub : 0);
                 unsigned GL[kBatchR];
                 const unsigned v = lane_setup<kBatchR>(ps, n, nse, sS, sLin, sC, 32, lane, GL);
                 const unsigned long long pbase = ps << nse;
