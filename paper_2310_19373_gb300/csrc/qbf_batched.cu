@@ -392,51 +392,79 @@ __device__ __forceinline__ double q_at_b(const void *Q, int dtype, int e)
 
 // FP64 canonical order (float Q) or exact int64 (integer Q) over the caller's
 // n_src variables; padded variables contribute exact zeros.
+// One warp per candidate: lane i forms row i of the canonical sum (Q_ii +
+// sum_{j>i, x_j} (Q_ij + Q_ji) in ascending j, as the oracle does), so the
+// rows' loads overlap, and lane 0 adds the rows in ascending i: the same
+// operations in the same order as a single thread, bit for bit.
 __global__ void batched_rescore_kernel(const BatchDesc *desc, const unsigned long long *cand_idx,
                                        const unsigned *cand_inst, const Counters *ctr,
                                        unsigned long long cap, unsigned long long *keys,
                                        unsigned long long *best_key, BatchInfoDev *info)
 {
     const unsigned long long count = ctr->cand < cap ? ctr->cand : cap;
-    for (unsigned long long e = blockIdx.x * (unsigned long long)blockDim.x + threadIdx.x;
-         e < count; e += (unsigned long long)gridDim.x * blockDim.x) {
+    const int lane = threadIdx.x & 31;
+    const unsigned long long warps = (unsigned long long)gridDim.x * (blockDim.x >> 5);
+    for (unsigned long long e = blockIdx.x * (unsigned long long)(blockDim.x >> 5) +
+                                (threadIdx.x >> 5);
+         e < count; e += warps) {
         const unsigned inst = cand_inst[e];
         const BatchDesc d = desc[inst];
         const unsigned long long x = cand_idx[e];
-        const int n = d.n_src;
+        const int n = d.n_src;  // <= 34: rows i = lane and lane + 32
         unsigned long long key;
         if (d.dtype == QBF_I32 || d.dtype == QBF_I16) {
-            long long acc = 0;
-            for (int i = 0; i < n; ++i) {
-                if (!((x >> i) & 1ull))
+            long long rw[2] = {0, 0};
+            for (int h = 0; h < 2; ++h) {
+                const int i = lane + 32 * h;
+                if (i >= n || !((x >> i) & 1ull))
                     continue;
                 long long row = (long long)q_at_b(d.Q, d.dtype, i * n + i);
-                for (int j = i + 1; j < n; ++j)
+                for (int j = i + 1; j < n; ++j) {
+                    const long long a = (long long)q_at_b(d.Q, d.dtype, i * n + j) +
+                                        (long long)q_at_b(d.Q, d.dtype, j * n + i);
                     if ((x >> j) & 1ull)
-                        row += (long long)q_at_b(d.Q, d.dtype, i * n + j) +
-                               (long long)q_at_b(d.Q, d.dtype, j * n + i);
-                acc += row;
+                        row += a;
+                }
+                rw[h] = row;
+            }
+            long long acc = 0;
+            for (int i = 0; i < n; ++i) {
+                const long long r = __shfl_sync(0xffffffffu, (i >> 5) ? rw[1] : rw[0], i & 31);
+                if ((x >> i) & 1ull)
+                    acc += r;
             }
             key = key_of_int(acc);
         } else {
-            double acc = 0.0;
-            for (int i = 0; i < n; ++i) {
-                if (!((x >> i) & 1ull))
+            double rw[2] = {0.0, 0.0};
+            for (int h = 0; h < 2; ++h) {
+                const int i = lane + 32 * h;
+                if (i >= n || !((x >> i) & 1ull))
                     continue;
                 double row = q_at_b(d.Q, d.dtype, i * n + i);
-                for (int j = i + 1; j < n; ++j)
+                for (int j = i + 1; j < n; ++j) {
+                    const double a =
+                        __dadd_rn(q_at_b(d.Q, d.dtype, i * n + j), q_at_b(d.Q, d.dtype, j * n + i));
                     if ((x >> j) & 1ull)
-                        row = __dadd_rn(row, __dadd_rn(q_at_b(d.Q, d.dtype, i * n + j),
-                                                       q_at_b(d.Q, d.dtype, j * n + i)));
-                acc = __dadd_rn(acc, row);
+                        row = __dadd_rn(row, a);
+                }
+                rw[h] = row;
+            }
+            double acc = 0.0;
+            for (int i = 0; i < n; ++i) {
+                const double r = __shfl_sync(0xffffffffu, (i >> 5) ? rw[1] : rw[0], i & 31);
+                if ((x >> i) & 1ull)
+                    acc = __dadd_rn(acc, r);
             }
             key = key_of_double(acc);
         }
-        keys[e] = key;
-        atomicMin(&best_key[inst], key);
-        atomicAdd(&info[inst].ncand, 1ull);
+        if (lane == 0) {
+            keys[e] = key;
+            atomicMin(&best_key[inst], key);
+            atomicAdd(&info[inst].ncand, 1ull);
+        }
     }
 }
+
 
 // Suffix tables of the table-driven deferred walk: F(gray(t)) for t <
 // 2^(ns - 3) on the instance's image (int64 sums, exact in FP32 since the
