@@ -324,6 +324,33 @@ def run_profile_case(n, variant=0, prefix_bits=-1):
                       "argmin": sol.argmin, "walk_ms": sol.walk_seconds * 1e3}))
 
 
+def run_prefix_sweep(ns):
+    """MIN walk time of the table-driven deferred walk over prefix widths, for
+    FP32 Gaussian instances of each n (the planner's width reported beside)."""
+    import torch
+
+    import __graft_entry__
+
+    __graft_entry__.build()
+    from paper_2310_19373_gb300 import _binding as qb
+    from paper_2310_19373_gb300 import inputs
+
+    for n in ns:
+        Q = torch.from_numpy(inputs.config_n40_f32(0) if n == 40 else
+                             inputs.gaussian_f32(n, seed=n)).cuda()
+        auto = qb.solve(Q, timing=True)
+        row = {"n": n, "planner_prefix_bits": auto.prefix_bits, "walk_ms": {}}
+        for k in range(max(10, n - 24), min(28, n - 8) + 1):
+            ts = []
+            for _ in range(3):
+                s = qb.solve(Q, variant=qb.QBF_VARIANT_SPLIT_DEFER, prefix_bits=k, timing=True)
+                ts.append(s.walk_seconds)
+            if (s.min_value, s.argmin) != (auto.min_value, auto.argmin):
+                raise SystemExit(f"prefix sweep: n={n} k={k} changed the answer")
+            row["walk_ms"][k] = round(min(ts) * 1e3, 4)
+        print(json.dumps(row), flush=True)
+
+
 def run_profile_batched(count, variant=0):
     """Two batched solves on the first `count` instances of the 4096-instance
     workload (a small case for ncu)."""
@@ -574,6 +601,8 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-variants", action="store_true",
                     help="skip the batched / n=32 / n=20 lines reported beside the headline")
+    ap.add_argument("--prefix-sweep", default="",
+                    help="comma-separated n: time the deferred MIN walk over prefix widths and exit")
     ap.add_argument("--profile-n", type=int, default=0,
                     help="profiling target: two solves of an n-variable Gaussian FP32 instance, "
                          "no timing (for ncu)")
@@ -596,6 +625,9 @@ def main():
 
     if args.impl == "reference":
         run_reference(args, rank)
+        return
+    if args.prefix_sweep:
+        run_prefix_sweep([int(x) for x in args.prefix_sweep.split(",")])
         return
     if args.profile_n:
         run_profile_case(args.profile_n, VARIANTS[args.variant], args.prefix_bits)

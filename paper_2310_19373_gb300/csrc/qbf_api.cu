@@ -164,6 +164,28 @@ int auto_suffix_bits(int n)
     return ns;
 }
 
+// Suffix bits walked per lane by the table-driven deferred walk when the
+// caller leaves the prefix width to the planner (the lane's three group bits
+// come on top).  Measured on GB300 as the fastest MIN walk over the prefix
+// widths at n = 26..40: small problems want more lanes, large ones longer
+// lane walks, and from n = 36 on the lane depth of the n = 40 solve (for
+// example n = 26: 0.023 against 0.039 ms with 10 bits; n = 34: 0.93 against
+// 1.13 ms with 10 bits; n = 40: 16 bits, 53.0 ms, the fastest).
+int defer_suffix_bits(int n)
+{
+    if (n <= 27)
+        return 8;
+    if (n == 28)
+        return 9;
+    if (n <= 32)
+        return 11;
+    if (n <= 34)
+        return 12;
+    if (n == 35)
+        return 15;
+    return 16;
+}
+
 // walked blocks per thread (each 2^R states) are at most 2^kMaxBlockBits
 constexpr int kMaxBlockBits = 20;
 
@@ -205,7 +227,9 @@ int plan_geometry(int n, const qbf_options &o, Geo *g)
             if (k > n - 4 || k > 28)
                 return set_err(QBF_EINVAL, "prefix_bits must be in [0, min(n-4, 28)] for the eight-prefix walks");
         } else {
-            const int nsw = std::max(1, std::min(auto_suffix_bits(nf), nf - 3));
+            const int want = (o.variant == QBF_VARIANT_SPLIT_DEFER) ? defer_suffix_bits(nf)
+                                                                    : auto_suffix_bits(nf);
+            const int nsw = std::max(1, std::min(want, nf - 3));
             k = n - nsw - 3;
         }
     } else if (o.variant == QBF_VARIANT_SPLIT_F32) {
