@@ -43,31 +43,11 @@ __global__ void reset_counters_kernel(Counters *c)
     }
 }
 
-namespace {
-
-// Block-wide sum of a 64-bit count (blockDim.x multiple of 32, <= 1024).
-__device__ unsigned long long block_sum_u64(unsigned long long x, unsigned long long *sh)
-{
-    for (int o = 16; o > 0; o >>= 1)
-        x += __shfl_xor_sync(0xffffffffu, x, o);
-    const int w = threadIdx.x >> 5, nw = blockDim.x >> 5;
-    if ((threadIdx.x & 31) == 0)
-        sh[w] = x;
-    __syncthreads();
-    unsigned long long r = 0;
-    for (int i = 0; i < nw; ++i)
-        r += sh[i];
-    __syncthreads();
-    return r;
-}
-
-}  // namespace
 
 __global__ void __launch_bounds__(1024) threshold_kernel(const Plan *plan, const int *pmin,
                                                          unsigned long long npref, int top_k,
                                                          Counters *c)
 {
-    __shared__ unsigned long long sh[32];
     if (plan->status != QBF_OK)
         return;
     long long base;
@@ -78,64 +58,70 @@ __global__ void __launch_bounds__(1024) threshold_kernel(const Plan *plan, const
             c->tau = INT_MAX;
         return;
     } else {
-        // smallest b with #{p : pmin[p] <= b} >= top_k, by a 16-way search:
-        // each pass counts against 15 pivots that split [lo, hi] evenly
-        // (the answer stays in [lo, hi]; hi always has count >= top_k)
-        __shared__ unsigned cnt_w[32][15];
-        __shared__ unsigned long long tot_s[15];
-        __shared__ int range[2];
-        int lo = c->gmin, hi = INT_MAX;  // counts fit 32 bits: npref <= 2^28
-        const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
-        while (lo < hi) {
-            const long long span = (long long)hi - lo;
-            int piv[15];
-            unsigned cnt[15];
-#pragma unroll
-            for (int j = 0; j < 15; ++j) {
-                piv[j] = (int)(lo + (span * (j + 1)) / 16);
-                cnt[j] = 0;
-            }
-            for (unsigned long long e = threadIdx.x; e < npref; e += blockDim.x) {
-                const int v = pmin[e];
-#pragma unroll
-                for (int j = 0; j < 15; ++j)
-                    cnt[j] += (v <= piv[j]) ? 1u : 0u;
-            }
-#pragma unroll
-            for (int j = 0; j < 15; ++j) {
-                unsigned x = cnt[j];
-                for (int o = 16; o > 0; o >>= 1)
-                    x += __shfl_xor_sync(0xffffffffu, x, o);
-                if (lane == 0)
-                    cnt_w[wid][j] = x;
-            }
+        // smallest b with #{p : pmin[p] <= b} >= top_k: the top_k-th smallest
+        // prefix minimum, by a radix select on order-preserving keys (the
+        // sign bit flipped), 8 bits per pass from the top.  Each pass counts
+        // the keys that match the digits chosen so far by their next digit
+        // (a warp's equal digits in one shared add); the digit at which the
+        // running count reaches the remaining rank is kept.
+        __shared__ unsigned hist[256];
+        __shared__ unsigned sel[2];  // chosen digit, keys of the group below it
+        const int lane = threadIdx.x & 31;
+        unsigned prefix = 0, pmask = 0;
+        unsigned krem = (unsigned)top_k;  // rank within the matching group, 1-based
+        for (int shift = 24; shift >= 0; shift -= 8) {
+            for (int d = threadIdx.x; d < 256; d += blockDim.x)
+                hist[d] = 0;
             __syncthreads();
-            if (threadIdx.x < 15) {  // one thread per pivot sums the warps' counts
-                unsigned long long tot = 0;
-                for (int w = 0; w < nw; ++w)
-                    tot += cnt_w[w][threadIdx.x];
-                tot_s[threadIdx.x] = tot;
-            }
-            __syncthreads();
-            if (threadIdx.x == 0) {
-                // (pivots recomputed, not indexed, so piv[] stays in registers)
-                int nlo = (int)(lo + (span * 15) / 16) + 1, nhi = hi;
-                for (int j = 0; j < 15; ++j) {
-                    if (tot_s[j] >= (unsigned long long)top_k) {
-                        nhi = (int)(lo + (span * (j + 1)) / 16);
-                        nlo = j ? (int)(lo + (span * j) / 16) + 1 : lo;
-                        break;
-                    }
+            for (unsigned long long e0 = 0; e0 < npref; e0 += blockDim.x) {
+                const unsigned long long e = e0 + threadIdx.x;
+                const unsigned key = e < npref ? ((unsigned)pmin[e] ^ 0x80000000u) : 0u;
+                const bool take = e < npref && (key & pmask) == prefix;
+                const unsigned m = __ballot_sync(0xffffffffu, take);
+                if (take) {
+                    const unsigned d = (key >> shift) & 255u;
+                    const unsigned peers = __match_any_sync(m, d);
+                    if (lane == __ffs(peers) - 1)
+                        atomicAdd(&hist[d], (unsigned)__popc(peers));
                 }
-                range[0] = nlo;
-                range[1] = nhi;
             }
             __syncthreads();
-            lo = range[0];
-            hi = range[1];
+            if (threadIdx.x < 32) {
+                // lane L holds bins 8L .. 8L + 7; an inclusive scan of the lane
+                // totals finds the lane, then the lane its bin
+                unsigned b8[8], tot = 0;
+#pragma unroll
+                for (int q = 0; q < 8; ++q) {
+                    b8[q] = hist[lane * 8 + q];
+                    tot += b8[q];
+                }
+                unsigned inc = tot;
+#pragma unroll
+                for (int o = 1; o < 32; o <<= 1) {
+                    const unsigned y = __shfl_up_sync(0xffffffffu, inc, o);
+                    if (lane >= o)
+                        inc += y;
+                }
+                const unsigned below = inc - tot;
+                const unsigned hit = __ballot_sync(0xffffffffu, below < krem && inc >= krem);
+                if (lane == __ffs(hit) - 1) {
+                    unsigned c = below;
+                    int q = 0;
+                    while (c + b8[q] < krem) {
+                        c += b8[q];
+                        ++q;
+                    }
+                    sel[0] = (unsigned)(lane * 8 + q);
+                    sel[1] = c;
+                }
+            }
             __syncthreads();
+            prefix |= sel[0] << shift;
+            pmask |= 255u << shift;
+            krem -= sel[1];
+            __syncthreads();  // every thread has read sel before the next pass
         }
-        base = lo;
+        base = (long long)(int)(prefix ^ 0x80000000u);
     }
     if (threadIdx.x == 0) {
         long long t = base + plan->window;

@@ -64,16 +64,8 @@ __global__ void __launch_bounds__(kWalkThreads) walk_split_kernel(const Plan *__
     int *sS = smem;
     int *sLin = sS + n * n;
     int *sC = sLin + n;
-    for (int e = threadIdx.x; e < n * n; e += blockDim.x)
-        sS[e] = plan->S[e];
-    for (int e = threadIdx.x; e < n; e += blockDim.x)
-        sLin[e] = plan->lin[e];
-    __syncthreads();
     if (plan->status != QBF_OK)
         return;
-
-    const int lane = threadIdx.x & 31;
-    const int4 *rec4 = reinterpret_cast<const int4 *>(recs);
 
     unsigned long long nitems;
     unsigned long long total = 0;
@@ -88,6 +80,18 @@ __global__ void __launch_bounds__(kWalkThreads) walk_split_kernel(const Plan *__
     } else {
         nitems = a.nitems;
     }
+    // the EMIT grid is sized before the flagged count is known: blocks past
+    // the work leave before staging the image (the others drain every item)
+    if ((unsigned long long)blockIdx.x * (blockDim.x >> 5) >= nitems)
+        return;
+    for (int e = threadIdx.x; e < n * n; e += blockDim.x)
+        sS[e] = plan->S[e];
+    for (int e = threadIdx.x; e < n; e += blockDim.x)
+        sLin[e] = plan->lin[e];
+    __syncthreads();
+
+    const int lane = threadIdx.x & 31;
+    const int4 *rec4 = reinterpret_cast<const int4 *>(recs);
 
     const int tau = (MODE == kModeEmit) ? a.ctr->tau : 0;
 
