@@ -67,7 +67,7 @@ enum {
     QBF_EDTYPE = 3,     /* unknown dtype                                    */
     QBF_ECUDA = 4,      /* a CUDA call failed                               */
     QBF_EOVERFLOW = 5,  /* more candidate states than the scratch can hold  */
-    QBF_ECANCELED = 6,
+    QBF_ECANCELED = 6,  /* qbf_cancel() stopped the call; no result       */
     QBF_ENOTIMPL = 7,
     QBF_ERANGE = 8      /* integer Q whose sum |Q_ij| does not fit in int32 */
 };
@@ -569,6 +569,24 @@ int qbf_alu_microbench(int op, double *ops_per_clk_sm, double *sm_mhz, double *s
 
 /* Human-readable description of the last error on this thread. */
 const char *qbf_last_error_string(void);
+
+/*
+ * qbf_cancel -- stop the solve that is running, from any host thread.
+ *
+ * Sets a word of pinned, device-mapped host memory.  The walks read it each
+ * time a warp takes a work item, so they stop within one item's time: about
+ * 3 ms at n = 40 at the automatic prefix width.  The log Z walks read it
+ * when a block starts.  The running qbf_solve, qbf_solve_host,
+ * qubo_bf_solve, qbf_chunked_step, qbf_solve_batched(_info) or
+ * qbf_logz(_backward) then returns QBF_ECANCELED, with no result and its
+ * outputs unspecified.  A chunked run stays at its last completed step.
+ * Every such call clears the word when it starts, so a qbf_cancel with no
+ * call running has no effect.  A solve in the tensor-core form
+ * (QBF_VARIANT_TC) does not stop early: it runs to its end and then reports
+ * QBF_ECANCELED.  qbf_solve_noalloc and the prefix-minima and trace entry
+ * points ignore the word.  Always returns QBF_OK.
+ */
+int qbf_cancel(void);
 
 /* Free the library's scratch pools on every device it touched. */
 int qbf_release(void);

@@ -149,6 +149,7 @@ _SIGS = {
                                                      ctypes.c_uint64,
                                                      ctypes.POINTER(ctypes.c_uint64),
                                                      ctypes.POINTER(QbfBatchInfo), _VP]),
+    "qbf_cancel": (ctypes.c_int, []),
     "qbf_tune": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_char_p]),
     "qbf_tuned_params": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.POINTER(ctypes.c_int),
                                         ctypes.POINTER(ctypes.c_int)]),
@@ -349,6 +350,11 @@ def batched_item_minima(Qs, inst: int, max_items: int, batch_suffix_bits: int = 
     s = stream if stream is not None else torch.cuda.current_stream().cuda_stream
     return qbf_solve_batched_item_minima([q.data_ptr() for q in Qs], [q.shape[0] for q in Qs],
                                          [dtype_code(q) for q in Qs], opt, inst, max_items, s)
+
+
+def qbf_cancel() -> None:
+    """Stop the running solve from any thread (it returns QBF_ECANCELED)."""
+    _check(lib().qbf_cancel())
 
 
 def qbf_tune(n_min: int, n_max: int, dtype: int, cache_path: str | None = None) -> None:

@@ -499,6 +499,7 @@ int solve_one(const void *Q, bool host_q, int n, int dtype, const qbf_options *o
     char *h = (char *)P->host;
     const bool is_int = (dtype == QBF_I32 || dtype == QBF_I16);
     cudaEvent_t ev[2] = {nullptr, nullptr};
+    cancel_clear();
     // Every stream operation of one attempt, on stream st: replayable as a
     // graph (no host decision inside; the host reads the results afterwards)
     auto enqueue = [&](cudaStream_t s) -> int {
@@ -514,6 +515,7 @@ int solve_one(const void *Q, bool host_q, int n, int dtype, const qbf_options *o
     // A2-A4: MIN walk over every prefix
     WalkArgs a;
     memset(&a, 0, sizeof(a));
+    a.cancel = cancel_word_dev();
     a.n = n;
     a.ns = g.ns;
     a.p_lo = g.p_lo;
@@ -614,6 +616,13 @@ int solve_one(const void *Q, bool host_q, int n, int dtype, const qbf_options *o
         return rc;
     }
     QBF_CUDA(cudaStreamSynchronize(s), "solve");
+    if (cancel_requested()) {
+        if (o.timing) {
+            cudaEventDestroy(ev[0]);
+            cudaEventDestroy(ev[1]);
+        }
+        return set_err(QBF_ECANCELED, "cancelled by qbf_cancel");
+    }
     float walk_ms = 0.f;
     if (o.timing) {
         cudaEventElapsedTime(&walk_ms, ev[0], ev[1]);
@@ -755,6 +764,56 @@ namespace qbf {
 // Lets other translation units of the library report errors through
 // qbf_last_error_string().
 int record_error(int code, const char *msg) { return set_err(code, msg); }
+
+namespace {
+std::mutex g_cancel_mu;
+int *g_cancel = nullptr;  // pinned, mapped into every device's address space
+const volatile int *g_cancel_dev = nullptr;
+bool g_cancel_tried = false;
+
+// Allocates the word once (outside any stream capture: the solves call
+// cancel_clear before they enqueue or capture their work).
+void cancel_alloc_locked()
+{
+    if (g_cancel || g_cancel_tried)
+        return;
+    g_cancel_tried = true;
+    void *p = nullptr, *d = nullptr;
+    if (cudaHostAlloc(&p, sizeof(int), cudaHostAllocMapped | cudaHostAllocPortable) !=
+        cudaSuccess) {
+        cudaGetLastError();
+        return;  // no cancellation; the solves still run
+    }
+    if (cudaHostGetDevicePointer(&d, p, 0) != cudaSuccess) {
+        cudaGetLastError();
+        cudaFreeHost(p);
+        return;
+    }
+    g_cancel = static_cast<int *>(p);
+    g_cancel_dev = static_cast<const volatile int *>(d);
+    __atomic_store_n(g_cancel, 0, __ATOMIC_SEQ_CST);
+}
+}  // namespace
+
+const volatile int *cancel_word_dev()
+{
+    std::lock_guard<std::mutex> lk(g_cancel_mu);
+    return g_cancel_dev;  // no CUDA call: safe inside a stream capture
+}
+
+void cancel_clear()
+{
+    std::lock_guard<std::mutex> lk(g_cancel_mu);
+    cancel_alloc_locked();
+    if (g_cancel)
+        __atomic_store_n(g_cancel, 0, __ATOMIC_SEQ_CST);
+}
+
+bool cancel_requested()
+{
+    std::lock_guard<std::mutex> lk(g_cancel_mu);
+    return g_cancel && __atomic_load_n(g_cancel, __ATOMIC_SEQ_CST) != 0;
+}
 }  // namespace qbf
 
 extern "C" {
@@ -1276,6 +1335,14 @@ int qbf_danskin(const uint64_t *argmin_host, int n, int batch, const double *ups
 }
 
 const char *qbf_last_error_string(void) { return g_err.c_str(); }
+
+int qbf_cancel(void)
+{
+    std::lock_guard<std::mutex> lk(g_cancel_mu);
+    if (g_cancel)
+        __atomic_store_n(g_cancel, 1, __ATOMIC_SEQ_CST);
+    return QBF_OK;
+}
 
 int qbf_release(void)
 {

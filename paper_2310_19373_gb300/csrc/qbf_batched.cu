@@ -97,6 +97,7 @@ struct BatchArgs {
     unsigned *cand_inst;
     unsigned long long cap;
     const float *ftab;  // suffix tables of the table-driven deferred walk
+    const volatile int *cancel;  // nullptr, or the cancellation word
     int mix;  // MIN walk for instances whose image fits 2^23: 0 none (int32),
               // 1 the two-pipe walk, 2 the deferred-correction walk
 };
@@ -159,7 +160,7 @@ __global__ void __launch_bounds__(kBatchThreads, (MODE == kModeMin && MIXK == 2)
     while (true) {
         unsigned long long g = 0;
         if (lane == 0)
-            g = atomicAdd(&a.ctr->items[MODE], 1ull);
+            g = cancelled(a.cancel) ? total : atomicAdd(&a.ctr->items[MODE], 1ull);
         g = __shfl_sync(0xffffffffu, g, 0);
         if (g >= total)
             break;
@@ -751,6 +752,7 @@ int enqueue_batch(BatchState &B, const BLayout &L, const BStage &S, int count,
     a.cap = kBatchCandCap;
     a.mix = mix;
     a.ftab = (const float *)(d + L.ftab);
+    a.cancel = cancel_word_dev();
     if (mix == 2)
         batched_walk_kernel<kModeMin, 2><<<grid_min, kBatchThreads, 0, s>>>(a);
     else if (mix == 1)
@@ -919,6 +921,7 @@ int solve_batched_mode(const void *const *Q, const int *n, const int *dtype, int
     char *h = (char *)B.host;
     // the previous replay may still read the staging buffer: wait for it
     B_CUDA(cudaStreamSynchronize(s), "batch stream");
+    cancel_clear();
     memcpy(h + S.desc, desc.data(), sizeof(BatchDesc) * count);
 
     GraphKey key;
@@ -952,6 +955,8 @@ int solve_batched_mode(const void *const *Q, const int *n, const int *dtype, int
     }
     B_CUDA(cudaGraphLaunch(B.exec, s), "graph launch");
     B_CUDA(cudaStreamSynchronize(s), "batched solve");
+    if (cancel_requested())
+        return record_error(QBF_ECANCELED, "cancelled by qbf_cancel");
     if (kernel_launches)
         *kernel_launches = (mix == 2) ? 12 : 11;
 

@@ -30,6 +30,7 @@ struct WalkArgs {
     unsigned long long cand_cap;
     unsigned long long *trace_idx;  // TRACE
     long long *trace_val;
+    const volatile int *cancel;     // nullptr, or the cancellation word
 };
 
 // qbf_prepare.cu
@@ -64,6 +65,12 @@ __global__ void select_kernel(const Plan *plan, const unsigned long long *cand,
 
 // qbf_api.cu: report an error through qbf_last_error_string(); returns code
 int record_error(int code, const char *msg);
+// qbf_api.cu: the cancellation word (pinned, device-mapped host memory,
+// allocated on first use; nullptr if that failed).  A solve clears it when it
+// starts and reports QBF_ECANCELED if it is set when the solve's work is done.
+const volatile int *cancel_word_dev();
+void cancel_clear();
+bool cancel_requested();
 
 // qbf_batched.cu
 // Where a batched solve copies the MIN pass's per-item minima of one instance

@@ -64,6 +64,7 @@ struct LzArgs {
     const int *shift;           // per instance and walk: (hi, lo) value of the argmin
     const float2 *cc;           // [b][kLzMaxBeta]: (c_hi, c_lo) of each beta
     float lo_scale;             // 2^-L: weight of the lo limb
+    const volatile int *cancel; // nullptr, or the cancellation word
     int beta0;                  // first beta of this launch
     double *laneZ;              // MODE Z:  [b][lane][beta]
     double *laneM1;             // MODE M1: [b][lane][ns]
@@ -173,8 +174,11 @@ __global__ void __launch_bounds__(kLzThreads) logz_walk_kernel(LzArgs a)
     for (int e = threadIdx.x; e < 128; e += blockDim.x) {
         sK2[e] = make_int2(a.K[pidx * 128 + e], a.K[(pidx + 1) * 128 + e]);
     }
+    __shared__ int s_stop;  // read once per block, so the block leaves as one
+    if (threadIdx.x == 0)
+        s_stop = cancelled(a.cancel);
     __syncthreads();
-    if (ph->status != QBF_OK)
+    if (ph->status != QBF_OK || s_stop)
         return;
     const unsigned long long p = p0 + threadIdx.x;
     const bool active = p < a.lanes;
@@ -840,6 +844,7 @@ LzArgs lz_args(const LzGeo &g, char *base, const LzLayout &L, int walk, int nbet
     a.laneM1 = (double *)(base + L.laneM1);
     a.cc = (const float2 *)(base + L.cc);
     a.lo_scale = (float)ldexp(1.0, -logz_lo_bits(g.n));
+    a.cancel = cancel_word_dev();
     a.beta0 = 0;
     (void)beta;
     return a;
@@ -899,6 +904,8 @@ int logz_forward(const void *Q, int n, int dtype, int batch, const double *beta,
     L_CUDA(cudaMemcpyAsync(logz, dlogz, sizeof(double) * batch * nbeta, cudaMemcpyDeviceToHost, s),
            "log Z download");
     L_CUDA(cudaStreamSynchronize(s), "log Z");
+    if (cancel_requested())
+        return record_error(QBF_ECANCELED, "cancelled by qbf_cancel");
     return QBF_OK;
 }
 
@@ -947,6 +954,8 @@ int logz_backward(const void *Q, int n, int dtype, int batch, const double *beta
         }
     }
     L_CUDA(cudaStreamSynchronize(s), "log Z backward");
+    if (cancel_requested())
+        return record_error(QBF_ECANCELED, "cancelled by qbf_cancel");
     return QBF_OK;
 }
 

@@ -77,7 +77,7 @@ __global__ void __launch_bounds__(kWalkThreads, 3)
     while (true) {
         unsigned long long item = 0;
         if (lane == 0)
-            item = atomicAdd(&a.ctr->items[kModeMin], 1ull);
+            item = cancelled(a.cancel) ? a.nitems : atomicAdd(&a.ctr->items[kModeMin], 1ull);
         item = __shfl_sync(0xffffffffu, item, 0);
         if (item >= a.nitems)
             break;
@@ -191,7 +191,7 @@ __global__ void __launch_bounds__(kDefer2Threads, kDefer2CtasPerSm)
     while (true) {
         unsigned long long item = 0;
         if (lane == 0)
-            item = atomicAdd(&a.ctr->items[kModeMin], 1ull);
+            item = cancelled(a.cancel) ? a.nitems : atomicAdd(&a.ctr->items[kModeMin], 1ull);
         item = __shfl_sync(0xffffffffu, item, 0);
         if (item >= a.nitems)
             break;

@@ -89,7 +89,7 @@ __device__ __forceinline__ bool next_item(const WalkArgs &a, int lane, unsigned 
 {
     unsigned long long item = 0;
     if (lane == 0)
-        item = atomicAdd(&a.ctr->items[kModeMin], 1ull);
+        item = cancelled(a.cancel) ? a.nitems : atomicAdd(&a.ctr->items[kModeMin], 1ull);
     item = __shfl_sync(0xffffffffu, item, 0);
     if (item >= a.nitems)
         return false;
