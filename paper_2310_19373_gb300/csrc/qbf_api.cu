@@ -107,6 +107,9 @@ int pool_get(size_t bytes, size_t hbytes, Pool **out)
         g_pools.resize(dev + 1);
     Pool &P = g_pools[dev];
     if (P.bytes < bytes) {
+        if (inject_alloc_failure())
+            return set_err(QBF_ECUDA, "cudaMalloc(scratch): failure injected by "
+                                      "QBF_INJECT_ALLOC_FAILURE");
         if (P.dev) {
             QBF_CUDA(cudaDeviceSynchronize(), "cudaDeviceSynchronize");
             cudaFree(P.dev);
@@ -453,6 +456,7 @@ void release_graphs()
 int solve_one(const void *Q, bool host_q, int n, int dtype, const qbf_options *opt_in,
               qbf_result *out, cudaStream_t s)
 {
+    const NvtxRange range("qbf_solve");
     int rc = check_common(Q, n, dtype, out);
     if (rc)
         return rc;

@@ -804,6 +804,7 @@ int solve_batched_mode(const void *const *Q, const int *n, const int *dtype, int
                        cudaStream_t s, int *kernel_launches, int mix, qbf_batch_info *info_out,
                        int ctas_override, const BatchItemsOut *items_out)
 {
+    const NvtxRange range("qbf_solve_batched");
     if (!Q || !n || !dtype || !min_value || !argmin)
         return record_error(QBF_EINVAL, "null pointer argument");
     if (count < 1 || count > QBF_BATCH_MAX_COUNT)
@@ -876,6 +877,9 @@ int solve_batched_mode(const void *const *Q, const int *n, const int *dtype, int
     const BStage S = bstage(count);
     bool relayout = false;
     if (B.dev_bytes < L.total) {
+        if (inject_alloc_failure())
+            return record_error(QBF_ECUDA, "cudaMalloc(batch scratch): failure injected by "
+                                           "QBF_INJECT_ALLOC_FAILURE");
         B_CUDA(cudaDeviceSynchronize(), "cudaDeviceSynchronize");
         if (B.dev)
             cudaFree(B.dev);

@@ -2,6 +2,9 @@
 #pragma once
 
 #include <cuda_runtime.h>
+#include <nvtx3/nvToolsExt.h>
+
+#include <cstdlib>
 
 #include "qbf_internal.cuh"
 
@@ -65,6 +68,20 @@ __global__ void select_kernel(const Plan *plan, const unsigned long long *cand,
 
 // qbf_api.cu: report an error through qbf_last_error_string(); returns code
 int record_error(int code, const char *msg);
+// A named NVTX range over one library call (host side; a profiler that
+// records NVTX shows each call's kernels under it, a no-op otherwise).
+struct NvtxRange {
+    explicit NvtxRange(const char *name) { nvtxRangePushA(name); }
+    ~NvtxRange() { nvtxRangePop(); }
+    NvtxRange(const NvtxRange &) = delete;
+    NvtxRange &operator=(const NvtxRange &) = delete;
+};
+
+// Host-side fault injection for the error paths: with the environment
+// variable QBF_INJECT_ALLOC_FAILURE set, a scratch pool that has to grow
+// reports a failed allocation instead of allocating (no GPU work involved).
+inline bool inject_alloc_failure() { return std::getenv("QBF_INJECT_ALLOC_FAILURE") != nullptr; }
+
 // qbf_api.cu: the cancellation word (pinned, device-mapped host memory,
 // allocated on first use; nullptr if that failed).  A solve clears it when it
 // starts and reports QBF_ECANCELED if it is set when the solve's work is done.

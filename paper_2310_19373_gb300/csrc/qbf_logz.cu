@@ -876,6 +876,7 @@ int lz_consts(const LzLayout &L, char *base, int batch, const double *beta, int 
 int logz_forward(const void *Q, int n, int dtype, int batch, const double *beta, int nbeta,
                  double *logz, double *min_value, uint64_t *argmin, cudaStream_t s)
 {
+    const NvtxRange range("qbf_logz_forward");
     int rc = lz_check(Q, n, dtype, batch, beta, nbeta);
     if (rc)
         return rc;
@@ -912,6 +913,7 @@ int logz_forward(const void *Q, int n, int dtype, int batch, const double *beta,
 int logz_backward(const void *Q, int n, int dtype, int batch, const double *beta, int nbeta,
                   const double *upstream, double *grad, double *moment, cudaStream_t s)
 {
+    const NvtxRange range("qbf_logz_backward");
     int rc = lz_check(Q, n, dtype, batch, beta, nbeta);
     if (rc)
         return rc;
