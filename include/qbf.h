@@ -136,7 +136,7 @@ typedef struct {
     int prefix_bits;    /* k actually used                                  */
     int suffix_bits;    /* n - k                                            */
     int variant;        /* walk kernel actually used                        */
-    int walk_launches;  /* launches of the main walk kernel in this call    */
+    int walk_launches;  /* launches of the MIN walk kernel in this call     */
     double walk_seconds;/* device time of the main walk kernel(s) when
                            opt->timing was set, else 0                      */
     int kernel_launches;/* kernels this call launched                       */
@@ -159,9 +159,13 @@ void qbf_default_options(qbf_options *opt);
  * of the best is rescored with the FP64 canonical sum, so the reported min
  * and argmin are those of the FP64 canonical objective.  Integer Q is walked
  * exactly (QBF_ERANGE when sum |Q_ij| >= 2^31).
+ * A walk over more than 2^41 states (n > 41 without fix_bits) runs as several
+ * MIN launches over consecutive prefix slices of at most 2^41 states, about
+ * 0.1 s each, so no kernel runs for seconds; out->walk_launches reports how
+ * many (the tensor-core form always uses one).
  * Errors: QBF_EINVAL, QBF_EDTYPE, QBF_ENONFINITE, QBF_ERANGE, QBF_EOVERFLOW
  * (the certification window holds more than 2^22 states, e.g. massive exact
- * ties with top_k > 1), QBF_ECUDA.
+ * ties with top_k > 1), QBF_ECANCELED (qbf_cancel), QBF_ECUDA.
  */
 int qbf_solve(const void *Q_dev, int n, int dtype, const qbf_options *opt, qbf_result *out,
               void *stream);

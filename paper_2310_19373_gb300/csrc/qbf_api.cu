@@ -189,6 +189,16 @@ int defer_suffix_bits(int n)
     return 16;
 }
 
+// Prefixes per launch of a MIN walk: all of them up to 2^41 states (the n = 40
+// solve is one launch), else slices of 2^41 states (multiples of 32 prefixes)
+constexpr unsigned long long kLaunchStates = 1ull << 41;
+unsigned long long launch_slice(unsigned long long npref, int ns)
+{
+    const unsigned long long per = ns >= 41 ? 1ull : kLaunchStates >> ns;
+    const unsigned long long cap = std::max(32ull, per / 32 * 32);
+    return npref <= cap ? npref : cap;
+}
+
 // walked blocks per thread (each 2^R states) are at most 2^kMaxBlockBits
 constexpr int kMaxBlockBits = 20;
 
@@ -503,6 +513,8 @@ int solve_one(const void *Q, bool host_q, int n, int dtype, const qbf_options *o
     char *h = (char *)P->host;
     const bool is_int = (dtype == QBF_I32 || dtype == QBF_I16);
     cudaEvent_t ev[2] = {nullptr, nullptr};
+    const unsigned long long slice = tc ? npref : launch_slice(npref, g.ns);
+    const int launches = (int)((npref + slice - 1) / slice);
     cancel_clear();
     // Every stream operation of one attempt, on stream st: replayable as a
     // graph (no host decision inside; the host reads the results afterwards)
@@ -517,46 +529,61 @@ int solve_one(const void *Q, bool host_q, int n, int dtype, const qbf_options *o
         return erc;
 
     // A2-A4: MIN walk over every prefix
-    WalkArgs a;
-    memset(&a, 0, sizeof(a));
-    a.cancel = cancel_word_dev();
-    a.n = n;
-    a.ns = g.ns;
-    a.p_lo = g.p_lo;
-    a.p_hi = g.p_hi;
-    a.nitems = (npref + 31) / 32;
-    a.ctr = ctr;
-    a.pmin = pmin;
+    WalkArgs a_all;
+    memset(&a_all, 0, sizeof(a_all));
+    a_all.cancel = cancel_word_dev();
+    a_all.n = n;
+    a_all.ns = g.ns;
+    a_all.p_lo = g.p_lo;
+    a_all.p_hi = g.p_hi;
+    a_all.nitems = (npref + 31) / 32;
+    a_all.ctr = ctr;
+    a_all.pmin = pmin;
     if (o.timing) {
         QBF_CUDA(cudaEventCreate(&ev[0]), "cudaEventCreate");
         QBF_CUDA(cudaEventCreate(&ev[1]), "cudaEventCreate");
         QBF_CUDA(cudaEventRecord(ev[0], s), "cudaEventRecord");
     }
-    if (tc)
-        QBF_CUDA(launch_tc_min(plan, n, g.p_lo, g.p_hi, pmin, ctr, num_sms(), s), "tc (min)");
-    else if (field)
-        QBF_CUDA(launch_walk_field(plan, a, num_sms(), s), "walk field (min)");
-    else if (naive)
-        QBF_CUDA(launch_walk_naive(plan, a, num_sms(), s), "naive (min)");
-    else if (defer)
-        QBF_CUDA(launch_walk_defer(g.R, plan, recs, a, (const int *)(base + L.kbuf),
-                                   base + L.kbuf + sizeof(int) * kKbufInts, num_sms(), s,
-                                   ftab ? (float *)(base + L.ftab) : nullptr),
-                 "walk defer (min)");
-    else if (mix)
-        QBF_CUDA(launch_walk_mix(g.R, plan, recs, a, (const int *)(base + L.kbuf),
-                                 (unsigned long long *)(base + L.kbuf + sizeof(int) * kKbufInts),
-                                 num_sms(), s),
-                 "walk mix (min)");
-    else if (f32)
-        QBF_CUDA(launch_walk_f32(g.R, plan, recs, a, (const int *)(base + L.kbuf),
-                                 (unsigned long long *)(base + L.kbuf + sizeof(int) * kKbufInts),
-                                 num_sms(), s),
-                 "walk f32 (min)");
-    else
-        QBF_CUDA(launch_walk(kModeMin, g.R, plan, recs, a,
-                             walk_grid(g.R, kModeMin, n, g.ns, a.nitems), s),
-                 "walk (min)");
+    // Long walks run as several launches over consecutive prefix slices of at
+    // most kLaunchStates states each (about 0.1 s of walking), so no single
+    // kernel runs for seconds; the work counter restarts for every slice and
+    // the global minimum accumulates across them.  The tensor-core form runs
+    // in one launch.
+    for (unsigned long long c0 = 0; c0 < npref; c0 += slice) {
+        WalkArgs a = a_all;
+        a.p_lo = g.p_lo + c0;
+        a.p_hi = std::min(g.p_hi, a.p_lo + slice);
+        a.nitems = (a.p_hi - a.p_lo + 31) / 32;
+        a.pmin = pmin + c0;
+        if (c0 > 0)
+            QBF_CUDA(cudaMemsetAsync(&ctr->items[kModeMin], 0, sizeof(ctr->items[kModeMin]), s),
+                     "restart the work counter");
+        if (tc)
+            QBF_CUDA(launch_tc_min(plan, n, g.p_lo, g.p_hi, pmin, ctr, num_sms(), s), "tc (min)");
+        else if (field)
+            QBF_CUDA(launch_walk_field(plan, a, num_sms(), s), "walk field (min)");
+        else if (naive)
+            QBF_CUDA(launch_walk_naive(plan, a, num_sms(), s), "naive (min)");
+        else if (defer)
+            QBF_CUDA(launch_walk_defer(g.R, plan, recs, a, (const int *)(base + L.kbuf),
+                                       base + L.kbuf + sizeof(int) * kKbufInts, num_sms(), s,
+                                       ftab ? (float *)(base + L.ftab) : nullptr),
+                     "walk defer (min)");
+        else if (mix)
+            QBF_CUDA(launch_walk_mix(g.R, plan, recs, a, (const int *)(base + L.kbuf),
+                                     (unsigned long long *)(base + L.kbuf + sizeof(int) * kKbufInts),
+                                     num_sms(), s),
+                     "walk mix (min)");
+        else if (f32)
+            QBF_CUDA(launch_walk_f32(g.R, plan, recs, a, (const int *)(base + L.kbuf),
+                                     (unsigned long long *)(base + L.kbuf + sizeof(int) * kKbufInts),
+                                     num_sms(), s),
+                     "walk f32 (min)");
+        else
+            QBF_CUDA(launch_walk(kModeMin, g.R, plan, recs, a,
+                                 walk_grid(g.R, kModeMin, n, g.ns, a.nitems), s),
+                     "walk (min)");
+    }
     if (o.timing)
         QBF_CUDA(cudaEventRecord(ev[1], s), "cudaEventRecord");
 
@@ -571,7 +598,7 @@ int solve_one(const void *Q, bool host_q, int n, int dtype, const qbf_options *o
         flag_kernel<<<fb, 256, 0, s>>>(plan, pmin, npref, o.top_k, flagged, ctr);
         QBF_CUDA(cudaGetLastError(), "flag_kernel");
     }
-    WalkArgs e = a;
+    WalkArgs e = a_all;
     e.ns = g.ns - g.q;
     e.q = g.q;
     e.top_k = o.top_k;
@@ -676,10 +703,12 @@ int solve_one(const void *Q, bool host_q, int n, int dtype, const qbf_options *o
                    : field ? QBF_VARIANT_FIELD
                    : naive ? QBF_VARIANT_NAIVE
                            : QBF_VARIANT_SPLIT;
-    out->walk_launches = 1;
+    out->walk_launches = launches;
     // prepare, tables, reset, walk(min), threshold, flag, walk(emit), rescore, select
     // (+ the correction-pair conversion of the packed walk)
-    out->kernel_launches = f32 ? 10 : 9;  // the FP32-pipe walks convert the correction pairs
+    // the FP32-pipe walks convert the correction pairs (or build the suffix
+    // table) before every MIN launch
+    out->kernel_launches = (f32 ? 10 : 9) + (launches - 1) * (f32 ? 2 : 1);
     out->walk_seconds = walk_ms * 1e-3;
     return QBF_OK;
 }

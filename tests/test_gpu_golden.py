@@ -92,3 +92,13 @@ def test_n44_chunked_top8_equals_oracle():
     r = c.result()
     assert (r.min_value, r.argmin) == (g["min"], g["argmin"])
     assert [[v, i] for v, i in zip(r.topk_values, r.topk_indices)] == g["topk"]
+
+
+def test_n44_single_call_walks_in_slices_and_equals_oracle():
+    """n = 44 in one qbf_solve: 2^44 states walked as 8 MIN launches of 2^41
+    states over consecutive prefix slices; the top-8 equals the oracle's."""
+    g = _golden("gaussian_n44_f32.json")
+    s = qb.solve(dev(inputs.gaussian_f32(44, seed=44)), top_k=8)
+    assert s.walk_launches == 8
+    assert (s.min_value, s.argmin) == (g["min"], g["argmin"])
+    assert [[v, i] for v, i in zip(s.topk_values, s.topk_indices)] == g["topk"]
