@@ -577,18 +577,20 @@ const char *qbf_last_error_string(void);
 /*
  * qbf_cancel -- stop the solve that is running, from any host thread.
  *
- * Sets a word of pinned, device-mapped host memory.  The walks read it each
- * time a warp takes a work item, so they stop within one item's time: about
- * 3 ms at n = 40 at the automatic prefix width.  The log Z walks read it
- * when a block starts.  The running qbf_solve, qbf_solve_host,
- * qubo_bf_solve, qbf_chunked_step, qbf_solve_batched(_info) or
- * qbf_logz(_backward) then returns QBF_ECANCELED, with no result and its
- * outputs unspecified.  A chunked run stays at its last completed step.
- * Every such call clears the word when it starts, so a qbf_cancel with no
- * call running has no effect.  A solve in the tensor-core form
- * (QBF_VARIANT_TC) does not stop early: it runs to its end and then reports
- * QBF_ECANCELED.  qbf_solve_noalloc and the prefix-minima and trace entry
- * points ignore the word.  Always returns QBF_OK.
+ * Sets a host flag and, with the copy engine on a stream of its own, a flag
+ * word in the memory of every device that has run a solve, so the write
+ * lands while a solve's kernels run.  The walks read the word each time a
+ * warp takes a work item, so they stop within one item's time: about 3 ms
+ * at n = 40 at the automatic prefix width.  The log Z walks read it when a
+ * block starts.  The running qbf_solve, qbf_solve_host, qubo_bf_solve,
+ * qbf_chunked_step, qbf_solve_batched(_info) or qbf_logz(_backward) then
+ * returns QBF_ECANCELED, with no result and its outputs unspecified.  A
+ * chunked run stays at its last completed step.  Every such call clears the
+ * flags when it starts, so a qbf_cancel with no call running has no effect.
+ * A solve in the tensor-core form (QBF_VARIANT_TC) does not stop early: it
+ * runs to its end and then reports QBF_ECANCELED.  qbf_solve_noalloc and the
+ * prefix-minima and trace entry points ignore the flags.  Returns QBF_OK
+ * (a failed device write only delays the stop to the end of the call).
  */
 int qbf_cancel(void);
 

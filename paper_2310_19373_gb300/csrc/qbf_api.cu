@@ -519,6 +519,7 @@ int solve_one(const void *Q, bool host_q, int n, int dtype, const qbf_options *o
     // Every stream operation of one attempt, on stream st: replayable as a
     // graph (no host decision inside; the host reads the results afterwards)
     auto enqueue = [&](cudaStream_t s) -> int {
+    QBF_CUDA(cancel_reset_async(s), "clear the cancellation word");
     if (host_q) {
         QBF_CUDA(cudaMemcpyAsync(base + L.qcopy, Q, qbytes, cudaMemcpyHostToDevice, s),
                  "copy Q to device");
@@ -799,53 +800,99 @@ namespace qbf {
 int record_error(int code, const char *msg) { return set_err(code, msg); }
 
 namespace {
+// Cancellation: a host flag (set by qbf_cancel, read by the host after a
+// solve) and, per device, a flag word in device memory that the kernels read.
+// qbf_cancel writes the device words with the copy engine on a stream of its
+// own, so the write lands while a solve's kernels run; a solve clears its
+// device word in its own stream before its kernels.
 std::mutex g_cancel_mu;
-int *g_cancel = nullptr;  // pinned, mapped into every device's address space
-const volatile int *g_cancel_dev = nullptr;
-bool g_cancel_tried = false;
-
-// Allocates the word once (outside any stream capture: the solves call
-// cancel_clear before they enqueue or capture their work).
-void cancel_alloc_locked()
-{
-    if (g_cancel || g_cancel_tried)
-        return;
-    g_cancel_tried = true;
-    void *p = nullptr, *d = nullptr;
-    if (cudaHostAlloc(&p, sizeof(int), cudaHostAllocMapped | cudaHostAllocPortable) !=
-        cudaSuccess) {
-        cudaGetLastError();
-        return;  // no cancellation; the solves still run
-    }
-    if (cudaHostGetDevicePointer(&d, p, 0) != cudaSuccess) {
-        cudaGetLastError();
-        cudaFreeHost(p);
-        return;
-    }
-    g_cancel = static_cast<int *>(p);
-    g_cancel_dev = static_cast<const volatile int *>(d);
-    __atomic_store_n(g_cancel, 0, __ATOMIC_SEQ_CST);
-}
+int g_cancel_host = 0;
+struct CancelDev {
+    int *flag = nullptr;
+    cudaStream_t stream = nullptr;
+};
+std::vector<CancelDev> g_cancel_dev;  // by device
+const int g_one = 1;
 }  // namespace
 
 const volatile int *cancel_word_dev()
 {
     std::lock_guard<std::mutex> lk(g_cancel_mu);
-    return g_cancel_dev;  // no CUDA call: safe inside a stream capture
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev >= (int)g_cancel_dev.size()) {
+        cudaGetLastError();
+        return nullptr;
+    }
+    return g_cancel_dev[dev].flag;  // allocated by cancel_clear, outside any capture
 }
 
 void cancel_clear()
 {
     std::lock_guard<std::mutex> lk(g_cancel_mu);
-    cancel_alloc_locked();
-    if (g_cancel)
-        __atomic_store_n(g_cancel, 0, __ATOMIC_SEQ_CST);
+    __atomic_store_n(&g_cancel_host, 0, __ATOMIC_SEQ_CST);
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) {
+        cudaGetLastError();
+        return;
+    }
+    if ((int)g_cancel_dev.size() <= dev)
+        g_cancel_dev.resize(dev + 1);
+    CancelDev &C = g_cancel_dev[dev];
+    if (C.flag)
+        return;
+    int *f = nullptr;
+    cudaStream_t cs = nullptr;
+    if (cudaMalloc(&f, sizeof(int)) != cudaSuccess ||
+        cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking) != cudaSuccess ||
+        cudaMemset(f, 0, sizeof(int)) != cudaSuccess) {
+        cudaGetLastError();
+        if (f)
+            cudaFree(f);
+        if (cs)
+            cudaStreamDestroy(cs);
+        return;  // no cancellation on this device; the solves still run
+    }
+    C.flag = f;
+    C.stream = cs;
+}
+
+cudaError_t cancel_reset_async(cudaStream_t s)
+{
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess)
+        return e;
+    int *f = nullptr;
+    {
+        std::lock_guard<std::mutex> lk(g_cancel_mu);
+        if (dev < (int)g_cancel_dev.size())
+            f = g_cancel_dev[dev].flag;
+    }
+    return f ? cudaMemsetAsync(f, 0, sizeof(int), s) : cudaSuccess;
 }
 
 bool cancel_requested()
 {
+    return __atomic_load_n(&g_cancel_host, __ATOMIC_SEQ_CST) != 0;
+}
+
+int cancel_all()
+{
     std::lock_guard<std::mutex> lk(g_cancel_mu);
-    return g_cancel && __atomic_load_n(g_cancel, __ATOMIC_SEQ_CST) != 0;
+    __atomic_store_n(&g_cancel_host, 1, __ATOMIC_SEQ_CST);
+    int cur = 0;
+    cudaGetDevice(&cur);
+    for (size_t d = 0; d < g_cancel_dev.size(); ++d) {
+        CancelDev &C = g_cancel_dev[d];
+        if (!C.flag)
+            continue;
+        cudaSetDevice((int)d);
+        cudaMemcpyAsync(C.flag, &g_one, sizeof(int), cudaMemcpyHostToDevice, C.stream);
+        cudaStreamSynchronize(C.stream);
+    }
+    cudaSetDevice(cur);
+    cudaGetLastError();  // a failed write only delays the stop to the call's end
+    return QBF_OK;
 }
 }  // namespace qbf
 
@@ -1369,13 +1416,7 @@ int qbf_danskin(const uint64_t *argmin_host, int n, int batch, const double *ups
 
 const char *qbf_last_error_string(void) { return g_err.c_str(); }
 
-int qbf_cancel(void)
-{
-    std::lock_guard<std::mutex> lk(g_cancel_mu);
-    if (g_cancel)
-        __atomic_store_n(g_cancel, 1, __ATOMIC_SEQ_CST);
-    return QBF_OK;
-}
+int qbf_cancel(void) { return cancel_all(); }
 
 int qbf_release(void)
 {

@@ -159,8 +159,11 @@ __global__ void __launch_bounds__(kBatchThreads, (MODE == kModeMin && MIXK == 2)
 
     while (true) {
         unsigned long long g = 0;
-        if (lane == 0)
-            g = cancelled(a.cancel) ? total : atomicAdd(&a.ctr->items[MODE], 1ull);
+        if (lane == 0) {
+            g = atomicAdd(&a.ctr->items[MODE], 1ull);
+            if (cancelled(a.cancel))  // qbf_cancel: take no more items
+                g = total;
+        }
         g = __shfl_sync(0xffffffffu, g, 0);
         if (g >= total)
             break;
@@ -722,6 +725,7 @@ int enqueue_batch(BatchState &B, const BLayout &L, const BStage &S, int count,
     unsigned long long *best_key = (unsigned long long *)(d + L.best_key);
     unsigned long long *best_idx = (unsigned long long *)(d + L.best_idx);
 
+    B_CUDA(cancel_reset_async(s), "clear the cancellation word");
     B_CUDA(cudaMemcpyAsync(d + L.desc, h + S.desc, sizeof(BatchDesc) * count,
                            cudaMemcpyHostToDevice, s),
            "batch descriptors");

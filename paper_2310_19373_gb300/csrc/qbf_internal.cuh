@@ -38,9 +38,10 @@ __host__ __device__ constexpr int logz_lo_bits(int n)
     return 23 - c < 16 ? 23 - c : 16;
 }
 
-// Cancellation: a word of device-mapped host memory (qbf_cancel sets it).
-// A warp's lane 0 reads it whenever it takes a work item; once it is set the
-// warp takes no more, so every persistent walk ends at its current items.
+// Cancellation: a flag word in device memory (qbf_cancel writes it with the
+// copy engine while a solve runs).  A warp's lane 0 reads it whenever it takes
+// a work item; once it is set the warp takes no more, so every persistent walk
+// ends at its current items.
 __device__ __forceinline__ bool cancelled(const volatile int *cancel)
 {
     return cancel != nullptr && *cancel != 0;

@@ -82,12 +82,17 @@ struct NvtxRange {
 // reports a failed allocation instead of allocating (no GPU work involved).
 inline bool inject_alloc_failure() { return std::getenv("QBF_INJECT_ALLOC_FAILURE") != nullptr; }
 
-// qbf_api.cu: the cancellation word (pinned, device-mapped host memory,
-// allocated on first use; nullptr if that failed).  A solve clears it when it
-// starts and reports QBF_ECANCELED if it is set when the solve's work is done.
+// qbf_api.cu: cancellation.  cancel_clear (host, before a solve enqueues or
+// captures its work) clears the host flag and allocates the current device's
+// flag word; cancel_word_dev is that word (nullptr if it could not be
+// allocated); cancel_reset_async clears it in the solve's stream before the
+// kernels; cancel_requested tells the host after the solve whether
+// qbf_cancel was called meanwhile (then the call returns QBF_ECANCELED).
 const volatile int *cancel_word_dev();
 void cancel_clear();
+cudaError_t cancel_reset_async(cudaStream_t s);
 bool cancel_requested();
+int cancel_all();
 
 // qbf_batched.cu
 // Where a batched solve copies the MIN pass's per-item minima of one instance

@@ -184,7 +184,7 @@ __global__ void __launch_bounds__(256) rescore_kernel(const Plan *plan, const vo
     if (plan->status != QBF_OK)
         return;
     const unsigned long long count = c->cand < cap ? c->cand : cap;
-    if ((unsigned long long)blockIdx.x * blockDim.x >= count)
+    if ((unsigned long long)blockIdx.x * (blockDim.x >> 5) >= count)
         return;  // no candidate for this block (uniform over the block)
     const bool is_int = (dtype == QBF_I32 || dtype == QBF_I16);
     for (int e = threadIdx.x; e < n * n; e += blockDim.x) {
@@ -198,33 +198,88 @@ __global__ void __launch_bounds__(256) rescore_kernel(const Plan *plan, const vo
                 (i == j) ? q_at(Q, dtype, e) : __dadd_rn(q_at(Q, dtype, e), q_at(Q, dtype, j * n + i)));
     }
     __syncthreads();
-    for (unsigned long long e = blockIdx.x * (unsigned long long)blockDim.x + threadIdx.x;
-         e < count; e += (unsigned long long)gridDim.x * blockDim.x) {
+    const unsigned long long warps = (unsigned long long)gridDim.x * (blockDim.x >> 5);
+    if (count > warps) {
+        // many candidates: one thread each (throughput)
+        for (unsigned long long e = blockIdx.x * (unsigned long long)blockDim.x + threadIdx.x;
+             e < count; e += (unsigned long long)gridDim.x * blockDim.x) {
+            const unsigned long long x = cand[e];
+            if (is_int) {
+                long long acc = 0;
+                for (int i = 0; i < n; ++i) {
+                    if (!((x >> i) & 1ull))
+                        continue;
+                    long long row = sP[i * n + i];
+                    for (int j = i + 1; j < n; ++j)
+                        if ((x >> j) & 1ull)
+                            row += sP[i * n + j];
+                    acc += row;
+                }
+                vals[e] = acc;
+            } else {
+                double acc = 0.0;
+                for (int i = 0; i < n; ++i) {
+                    if (!((x >> i) & 1ull))
+                        continue;
+                    double row = __longlong_as_double(sP[i * n + i]);
+                    for (int j = i + 1; j < n; ++j)
+                        if ((x >> j) & 1ull)
+                            row = __dadd_rn(row, __longlong_as_double(sP[i * n + j]));
+                    acc = __dadd_rn(acc, row);
+                }
+                vals[e] = __double_as_longlong(acc);
+            }
+        }
+        return;
+    }
+    // few candidates: one warp each (latency).  Lane i forms rows i and
+    // i + 32 of the canonical sum (ascending j), and the rows are added in
+    // ascending i: the same operations in the same order as one thread
+    const int lane = threadIdx.x & 31;
+    for (unsigned long long e = blockIdx.x * (unsigned long long)(blockDim.x >> 5) +
+                                (threadIdx.x >> 5);
+         e < count; e += warps) {
         const unsigned long long x = cand[e];
         if (is_int) {
-            long long acc = 0;
-            for (int i = 0; i < n; ++i) {
-                if (!((x >> i) & 1ull))
+            long long rw[2] = {0, 0};
+            for (int h = 0; h < 2; ++h) {
+                const int i = lane + 32 * h;
+                if (i >= n || !((x >> i) & 1ull))
                     continue;
                 long long row = sP[i * n + i];
                 for (int j = i + 1; j < n; ++j)
                     if ((x >> j) & 1ull)
                         row += sP[i * n + j];
-                acc += row;
+                rw[h] = row;
             }
-            vals[e] = acc;
-        } else {
-            double acc = 0.0;
+            long long acc = 0;
             for (int i = 0; i < n; ++i) {
-                if (!((x >> i) & 1ull))
+                const long long r = __shfl_sync(0xffffffffu, (i >> 5) ? rw[1] : rw[0], i & 31);
+                if ((x >> i) & 1ull)
+                    acc += r;
+            }
+            if (lane == 0)
+                vals[e] = acc;
+        } else {
+            double rw[2] = {0.0, 0.0};
+            for (int h = 0; h < 2; ++h) {
+                const int i = lane + 32 * h;
+                if (i >= n || !((x >> i) & 1ull))
                     continue;
                 double row = __longlong_as_double(sP[i * n + i]);
                 for (int j = i + 1; j < n; ++j)
                     if ((x >> j) & 1ull)
                         row = __dadd_rn(row, __longlong_as_double(sP[i * n + j]));
-                acc = __dadd_rn(acc, row);
+                rw[h] = row;
             }
-            vals[e] = __double_as_longlong(acc);
+            double acc = 0.0;
+            for (int i = 0; i < n; ++i) {
+                const double r = __shfl_sync(0xffffffffu, (i >> 5) ? rw[1] : rw[0], i & 31);
+                if ((x >> i) & 1ull)
+                    acc = __dadd_rn(acc, r);
+            }
+            if (lane == 0)
+                vals[e] = __double_as_longlong(acc);
         }
     }
 }
@@ -271,6 +326,8 @@ __device__ __forceinline__ Key warp_min_key(Key k, bool is_int)
 
 }  // namespace
 
+constexpr int kSelWarpK = 16;  // top_k up to this: per-warp lists, then one merge
+
 __global__ void __launch_bounds__(1024) select_kernel(const Plan *plan,
                                                       const unsigned long long *cand,
                                                       const long long *vals, const Counters *c,
@@ -289,9 +346,72 @@ __global__ void __launch_bounds__(1024) select_kernel(const Plan *plan,
     }
     const bool is_int = (plan->dtype == QBF_I32 || plan->dtype == QBF_I16);
     const unsigned long long count = c->cand < cap ? c->cand : cap;
+    int r = 0;
+    if (top_k <= kSelWarpK) {
+        // Each warp takes the top_k smallest of its share of the candidates
+        // (lane-strided), one warp-wide minimum per rank, with no block
+        // barrier; warp 0 then merges the warps' ascending lists, one head
+        // per lane.  The same keys in the same order as the block-wide rounds
+        // below, with one barrier instead of three per rank.
+        __shared__ Key wl[32][kSelWarpK];
+        Key prev;
+        prev.ok = 0;
+        int got = 0;
+        for (; got < top_k; ++got) {
+            Key best;
+            best.v = 0;
+            best.i = 0;
+            best.ok = 0;
+            for (unsigned long long e = (unsigned long long)wid * 32 + lane; e < count;
+                 e += blockDim.x) {
+                Key k;
+                k.v = vals[e];
+                k.i = cand[e];
+                k.ok = 1;
+                if (prev.ok && !key_less(prev, k, is_int))
+                    continue;
+                if (key_less(k, best, is_int))
+                    best = k;
+            }
+            best = warp_min_key(best, is_int);
+            if (!best.ok)
+                break;
+            if (lane == 0)
+                wl[wid][got] = best;
+            prev = best;
+        }
+        for (int q = got + lane; q < kSelWarpK; q += 32)
+            wl[wid][q].ok = 0;  // past the end of this warp's list
+        __syncthreads();
+        if (wid == 0) {
+            int head = 0;  // lane L reads warp L's list
+            for (; r < top_k; ++r) {
+                Key k;
+                k.v = 0;
+                k.i = 0;
+                k.ok = 0;
+                if (lane < nw && head < top_k)
+                    k = wl[lane][head];
+                const Key w = warp_min_key(k, is_int);
+                if (!w.ok)
+                    break;
+                if (k.ok && k.i == w.i)
+                    ++head;  // candidates are distinct states: one lane holds w
+                if (lane == 0) {
+                    res->topk_value[r] = is_int ? (double)w.v : __longlong_as_double(w.v);
+                    res->topk_index[r] = w.i;
+                }
+            }
+            if (lane == 0) {
+                res->count = r;
+                res->n_candidates = c->cand;
+                res->status = (c->cand > cap) ? QBF_EOVERFLOW : QBF_OK;
+            }
+        }
+        return;
+    }
     Key prev;
     prev.ok = 0;
-    int r = 0;
     for (; r < top_k; ++r) {
         // the smallest key above the previous winner: per thread, per warp
         // (shuffles), then over the warps (warp 0)

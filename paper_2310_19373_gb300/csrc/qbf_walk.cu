@@ -97,8 +97,11 @@ __global__ void __launch_bounds__(kWalkThreads) walk_split_kernel(const Plan *__
 
     while (true) {
         unsigned long long item = 0;
-        if (lane == 0)
-            item = cancelled(a.cancel) ? nitems : atomicAdd(&a.ctr->items[MODE], 1ull);
+        if (lane == 0) {
+            item = atomicAdd(&a.ctr->items[MODE], 1ull);
+            if (cancelled(a.cancel))  // qbf_cancel: take no more items
+                item = nitems;
+        }
         item = __shfl_sync(0xffffffffu, item, 0);
         if (item >= nitems)
             break;

@@ -96,8 +96,11 @@ __global__ void __launch_bounds__(kWalkThreads) walk_f32x2_min_kernel(const Plan
 
     while (true) {
         unsigned long long item = 0;
-        if (lane == 0)
-            item = cancelled(a.cancel) ? a.nitems : atomicAdd(&a.ctr->items[kModeMin], 1ull);
+        if (lane == 0) {
+            item = atomicAdd(&a.ctr->items[kModeMin], 1ull);
+            if (cancelled(a.cancel))  // qbf_cancel: take no more items
+                item = a.nitems;
+        }
         item = __shfl_sync(0xffffffffu, item, 0);
         if (item >= a.nitems)
             break;

@@ -88,8 +88,11 @@ __device__ __forceinline__ bool next_item(const WalkArgs &a, int lane, unsigned 
                                           bool &active)
 {
     unsigned long long item = 0;
-    if (lane == 0)
-        item = cancelled(a.cancel) ? a.nitems : atomicAdd(&a.ctr->items[kModeMin], 1ull);
+    if (lane == 0) {
+        item = atomicAdd(&a.ctr->items[kModeMin], 1ull);
+        if (cancelled(a.cancel))  // qbf_cancel: take no more items
+            item = a.nitems;
+    }
     item = __shfl_sync(0xffffffffu, item, 0);
     if (item >= a.nitems)
         return false;
