@@ -262,7 +262,15 @@ int plan_geometry(int n, const qbf_options &o, Geo *g)
         if (k > n - 1 || k > 28)
             return set_err(QBF_EINVAL, "prefix_bits must be in [0, min(n-1, 28)]");
     } else {
-        k = n - auto_suffix_bits(nf);
+        // the int32 split walk: a top-1 solve of a small problem runs fastest
+        // with more, shorter lanes (whole-solve times measured on GB300: n = 16
+        // 71 against 83 us, n = 22 82 against 93 us with 10 suffix bits); a
+        // top-k solve keeps the wider suffix (n = 20 top-8: 101 us, against
+        // 110 us with 6 bits)
+        int ns = auto_suffix_bits(nf);
+        if (o.top_k <= 1 && nf <= 23)
+            ns = std::min(nf, std::max(6, nf - 14));
+        k = n - ns;
     }
     // prefixes are numbered in 32 bits downstream (flag lists): an automatic
     // geometry keeps at most 2^28 of them, like an explicit prefix_bits
