@@ -351,6 +351,28 @@ def run_prefix_sweep(ns):
         print(json.dumps(row), flush=True)
 
 
+def run_profile_small():
+    """Three solves each of the n = 32 int32 instance (top-1) and the n = 20
+    FP64 instance (top-8): small solves, whose time the fixed kernels around
+    the walk set (a case for an ncu launch list)."""
+    import torch
+
+    import __graft_entry__
+
+    __graft_entry__.build()
+    from paper_2310_19373_gb300 import _binding as qb
+    from paper_2310_19373_gb300 import inputs
+
+    Q32 = torch.from_numpy(inputs.config_n32_int(0)).cuda()
+    Q20 = torch.from_numpy(inputs.config_n20_f64(0)).cuda()
+    for _ in range(3):
+        s32 = qb.solve(Q32)
+        s20 = qb.solve(Q20, top_k=8)
+    torch.cuda.synchronize()
+    print(json.dumps({"profile_small": True, "n32_prefix_bits": s32.prefix_bits,
+                      "n20_prefix_bits": s20.prefix_bits, "n20_top8": s20.topk_indices}))
+
+
 def run_profile_batched(count, variant=0):
     """Two batched solves on the first `count` instances of the 4096-instance
     workload (a small case for ncu)."""
@@ -601,6 +623,8 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-variants", action="store_true",
                     help="skip the batched / n=32 / n=20 lines reported beside the headline")
+    ap.add_argument("--profile-small", action="store_true",
+                    help="run three n=32 int32 and three n=20 FP64 top-8 solves and exit")
     ap.add_argument("--prefix-sweep", default="",
                     help="comma-separated n: time the deferred MIN walk over prefix widths and exit")
     ap.add_argument("--profile-n", type=int, default=0,
@@ -625,6 +649,9 @@ def main():
 
     if args.impl == "reference":
         run_reference(args, rank)
+        return
+    if args.profile_small:
+        run_profile_small()
         return
     if args.prefix_sweep:
         run_prefix_sweep([int(x) for x in args.prefix_sweep.split(",")])
