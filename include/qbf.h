@@ -594,7 +594,9 @@ const char *qbf_last_error_string(void);
  */
 int qbf_cancel(void);
 
-/* Free the library's scratch pools on every device it touched. */
+/* Free the library's scratch pools, captured solve graphs and cancellation
+ * words on every device it touched (the next call allocates afresh).  Call
+ * it before resetting a device with cudaDeviceReset. */
 int qbf_release(void);
 
 /* Library version as an integer (major*10000 + minor*100 + patch). */

@@ -884,6 +884,28 @@ bool cancel_requested()
     return __atomic_load_n(&g_cancel_host, __ATOMIC_SEQ_CST) != 0;
 }
 
+void release_cancel()
+{
+    std::lock_guard<std::mutex> lk(g_cancel_mu);
+    int cur = 0;
+    cudaGetDevice(&cur);
+    for (size_t d = 0; d < g_cancel_dev.size(); ++d) {
+        CancelDev &C = g_cancel_dev[d];
+        if (!C.flag && !C.stream)
+            continue;
+        cudaSetDevice((int)d);
+        if (C.stream) {
+            cudaStreamSynchronize(C.stream);
+            cudaStreamDestroy(C.stream);
+        }
+        if (C.flag)
+            cudaFree(C.flag);
+        C = CancelDev();
+    }
+    cudaSetDevice(cur);
+    cudaGetLastError();
+}
+
 int cancel_all()
 {
     std::lock_guard<std::mutex> lk(g_cancel_mu);
@@ -1432,6 +1454,7 @@ int qbf_release(void)
     release_logz();
     std::lock_guard<std::mutex> lk(g_mu);
     release_graphs();
+    release_cancel();
     int cur = 0;
     cudaGetDevice(&cur);
     for (size_t d = 0; d < g_pools.size(); ++d) {

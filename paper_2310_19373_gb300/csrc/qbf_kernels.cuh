@@ -93,6 +93,7 @@ void cancel_clear();
 cudaError_t cancel_reset_async(cudaStream_t s);
 bool cancel_requested();
 int cancel_all();
+void release_cancel();  // frees every device's word and stream (qbf_release)
 
 // qbf_batched.cu
 // Where a batched solve copies the MIN pass's per-item minima of one instance

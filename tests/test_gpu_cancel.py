@@ -65,3 +65,22 @@ def test_cancel_stops_a_batched_solve():
     vmin, am = qb.solve_batched(small)
     for q, v, a in zip(small, vmin, am):
         assert (v, a) == oracle.brute_min(q.cpu().numpy())
+
+
+def test_release_frees_the_words_and_the_next_calls_rebuild_them():
+    small = inputs.gaussian_f32(20, seed=4)
+    qb.solve(dev(small))
+    qb.qbf_release()  # pools, graphs and cancellation words freed
+    s = qb.solve(dev(small))
+    assert (s.min_value, s.argmin) == oracle.brute_min(small)
+    Q = dev(inputs.gaussian_f32(44, seed=8))
+    torch.cuda.synchronize()
+    timer = threading.Timer(0.15, qb.qbf_cancel)
+    t0 = time.perf_counter()
+    timer.start()
+    with pytest.raises(qb.QbfError) as e:
+        qb.solve(Q)
+    dt = time.perf_counter() - t0
+    timer.join()
+    assert e.value.status == qb.QBF_ECANCELED
+    assert dt < 0.6, dt
